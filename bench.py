@@ -1,0 +1,306 @@
+"""Benchmark: gate-level re-simulation throughput on one GB300.
+
+One step = one full re-simulation of the benchmark workload (every gate of
+every level over every cycle, SAIF included): the 200k-gate, depth-60,
+10,000-cycle netlist of the "mid" recipe (4-input cells, geometric fanout,
+COND delays on XOR2/MUX2, 20% narrow pulses), synthetic and seeded.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line.  ``value`` is gate x cycle evaluations per second over
+the timed steps (CUDA events on the library's stream, inputs resident in HBM),
+``e2e`` the same metric through the C interface from host buffers (stimulus
+upload, simulation, SAIF read-back every step), ``roofline`` the propagation
+kernel's algorithmic HBM bandwidth against the measured copy peak, and
+``cpu_baseline`` the CPU oracle on a bounded sample of the same workload.
+``--impl reference`` times the CPU oracle as the reference arm.
+With ``--gpus N`` under torchrun every rank runs an independent replica
+(the path does not shard across GPUs); ``value`` sums all ranks' work over
+the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import multiprocessing as mp
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+WORKLOAD = "mid"
+SEED = 1
+METRIC = "gate*cycle evals/s"
+UNIT = "gate-cycles/s"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ----------------------------------------------------------- CPU oracle leg
+
+def _oracle_worker(args):
+    name, seed, windows = args
+    sys.path.insert(0, ROOT)
+    import gen
+    import oracle
+    wl = gen.make_workload(name, seed=seed)
+    sim = oracle.EventSim(wl.netlist, wl.delays, wl.stim, W=1)
+    t = time.perf_counter()
+    for w in windows:
+        sim.window(w)
+    return time.perf_counter() - t, len(windows) * wl.netlist.num_gates
+
+
+def cpu_oracle(seconds: float = 12.0, name: str = WORKLOAD, seed: int = SEED, cores: int | None = None):
+    """Time the event-driven oracle on a bounded sample of windows, spread
+    over the host cores with a spawn pool (one independent window per task).
+    Returns (gate-cycles/s, cores, sample description)."""
+    cores = cores or os.cpu_count() or 1
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(cores) as pool:
+        # calibrate on one core: time two windows
+        dt, gc = pool.map(_oracle_worker, [(name, seed, [0, 1])])[0]
+        per_window = dt / 2
+        per_core = max(1, int(seconds / max(per_window, 1e-6)))
+        C = {"tiny": 1000, "mid": 10_000, "large": 20_000}[name]
+        step = max(1, C // (per_core * cores))
+        jobs = [(name, seed, [(k * cores + c) * step % C for k in range(per_core)]) for c in range(cores)]
+        res = pool.map(_oracle_worker, jobs)
+    wall = max(r[0] for r in res)
+    work = sum(r[1] for r in res)
+    sample = (f"{per_core * cores} of {C} windows (every {step}th), {name} workload, "
+              f"{cores} processes x {per_core} windows, max worker time {wall:.1f} s")
+    return work / wall, cores, sample
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ["clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.active",
+              "clocks_event_reasons.hw_slowdown", "clocks_event_reasons.hw_thermal_slowdown",
+              "clocks_event_reasons.sw_thermal_slowdown", "clocks_event_reasons.sw_power_cap"]
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + ",".join(self.FIELDS),
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.thread.join(timeout=2)
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------- main
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    return world, rank, local
+
+
+def dist_max(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def dist_barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def run_reference(args, world, rank):
+    """The reference arm: the CPU oracle as it stands, on host cores."""
+    if rank != 0:
+        return
+    per_step = []
+    cores = os.cpu_count() or 1
+    sample = ""
+    for s in range(args.warmup + args.steps):
+        v, cores, sample = cpu_oracle(seconds=args.ref_seconds)
+        if s >= args.warmup:
+            per_step.append(v)
+    value = statistics.mean(per_step)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": None,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+            "data": "synthetic", "config": _config(args),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def _config(args):
+    return {"workload": "mid: 200k gates, depth 60, 512 inputs, 10,000 cycles of 1,000 ps, "
+                        "fanin 1-4, geometric fanout mean 2.5, toggle p=0.3, 5% pulses (20% narrow), "
+                        "COND on XOR2/MUX2, delays 2-120 ps, seed 1",
+            "gates": 200_000, "cycles": 10_000, "window_cycles": 1, "tile_items": args.tile,
+            "parallelism": f"replicas x{args.gpus}", "l2": "inputs larger than L2 (waveform store ~20 GB)"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--tile", type=int, default=256)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--ref-seconds", type=float, default=8.0)
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+
+    # the oracle's spawn pool starts before any GPU work in this process
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        v, cores, sample = cpu_oracle(seconds=args.cpu_seconds)
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+
+    import gen
+    import paper_2203_06117_gb300 as gs
+    gs.build()
+    device = local
+    wl = gen.make_workload(WORKLOAD, seed=SEED)
+    G, C = wl.netlist.num_gates, wl.stim.num_cycles
+    units = G * C
+    sim = gs.Simulator(wl.netlist, wl.delays, wl.stim, device=device)
+    opts = dict(window_cycles=1, tile_items=args.tile, time_kernels=1)
+    for _ in range(args.warmup):
+        sim.simulate(**opts)
+    dist_barrier(world)
+    dev_ms, prop_ms, algo, launches, prop_launches = [], [], [], 0, 0
+    with ClockSampler(device) as clk:
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            sim.simulate(**opts)
+            st = sim.stats()
+            dev_ms.append(st["device_ms"])
+            prop_ms.append(st["prop_ms"])
+            algo.append(st["algo_bytes"])
+            launches += st["kernel_launches"]
+            prop_launches += st["prop_launches"]
+        host_s = time.perf_counter() - t0
+    dist_barrier(world)
+    total_s = dist_max(sum(dev_ms) / 1e3, world)
+    value = units * args.steps * world / total_s
+    ms_per_step = total_s * 1e3 / args.steps
+    peak, peak_kind = _peaks()
+    achieved = (sum(algo) / (sum(prop_ms) / 1e3)) / 1e9
+    edges = st["edges"]
+
+    # end to end through the C interface from host buffers
+    e2e_times = []
+    stim = wl.stim
+    h2d = stim.init.nbytes + stim.edge_ptr.nbytes + stim.edge_time.nbytes
+    d2h = 2 * 8 * wl.netlist.num_nets
+    for k in range(args.e2e_steps + 1):
+        t = time.perf_counter()
+        gs.gatspi_set_stimulus(sim.ctx, stim.num_cycles, stim.cycle_ps, stim.init, stim.edge_ptr,
+                               stim.edge_time)
+        gs.gatspi_simulate(sim.ctx, window_cycles=1, tile_items=args.tile)
+        saif = sim.saif()
+        if k:
+            e2e_times.append(time.perf_counter() - t)
+    e2e_s = dist_max(statistics.median(e2e_times), world)
+    sim.close()
+
+    if rank != 0:
+        return
+    clocks = clk.summary()
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": _config(args),
+        "e2e": {"value": units * world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h)},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
+                     "kernel": "propagate_kernel",
+                     "algo_bytes_per_step": int(algo[-1]), "prop_ms_per_step": statistics.mean(prop_ms),
+                     "launches_per_step": prop_launches // args.steps},
+        "cpu_baseline": cpu,
+        "clocks": {k: clocks[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")},
+        "gpu_launches": int(launches),
+        "detail": {"edges_per_step": int(edges), "host_s": host_s, "clock_samples": clocks["samples"],
+                   "saif_tc_total": int(saif[2].sum())},
+    }
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

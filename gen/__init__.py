@@ -282,3 +282,66 @@ def random_small(seed: int, max_inputs: int = 4, max_gates: int = 12, max_cycles
             ptr.append(len(times))
     st = Stimulus(C, int(cycle_ps), init, np.asarray(ptr, np.int64), np.asarray(times, np.int32))
     return Workload(f"random_small_{seed}", nl, d, st, D, dict(seed=seed))
+
+
+# ------------------------------------------------ job streams (batched / served)
+
+
+def batched_workload(seed: int = 1, n_jobs: int = 64, n_netlists: int = 8, scale: float = 1.0):
+    """64 jobs over 8 netlists of 10k-500k gates (log-uniform, mid recipe,
+    depth by log-linear interpolation through (2k, 20), (200k, 60),
+    (2M, 120)); cycles log-normal (median 2,000, sigma 1) clipped to
+    [100, 20,000]; toggle probability uniform in [0.05, 0.5].  ``scale``
+    shrinks gates and cycles for tests."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    nets = []
+    for k in range(n_netlists):
+        G = int(10 ** rng.uniform(np.log10(10_000), np.log10(500_000)) * scale)
+        G = max(G, 200)
+        D = min(interp_depth(G), G)
+        I = max(16, G // 400)
+        nets.append(make_workload("mid", seed=seed * 100 + k, num_gates=G, depth=D, num_inputs=I,
+                                      num_cycles=1))
+    reqs = []
+    for j in range(n_jobs):
+        n = int(rng.integers(0, n_netlists))
+        C = int(np.clip(np.exp(rng.normal(np.log(2000), 1.0)), 100, 20_000) * scale)
+        C = max(C, 2)
+        p = int(rng.uniform(50, 500))
+        st = make_stimulus(nets[n].netlist.num_inputs, C, seed * 10_000 + j, p, 50, 200,
+                               first_fanout_min_delay(nets[n].netlist, nets[n].delays))
+        reqs.append(dict(arrival=0.0, netlist=n, stim=st))
+    return nets, reqs
+
+
+def served_workload(seed: int = 1, rate: float = 200.0, seconds: float = 2.0, scale: float = 1.0,
+                    sizes=(50_000, 200_000, 500_000, 1_000_000)):
+    """Four resident netlists (50k, 200k, 500k, 1M gates; the tiny recipe's
+    cells and delays; depth interpolated), Poisson arrivals at ``rate``/s,
+    window cycles log-uniform in [100, 5,000], 30% of requests with a delay
+    edit re-timing 1% of gates by +-[10, 50] ps."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    nets = []
+    for k, G0 in enumerate(sizes):
+        G = max(200, int(G0 * scale))
+        D = min(interp_depth(G), G)
+        I = max(16, G // 400)
+        nets.append(make_workload("tiny", seed=seed * 100 + k, num_gates=G, depth=D, num_inputs=I,
+                                      num_cycles=1))
+    reqs = []
+    t = 0.0
+    while True:
+        t += rng.exponential(1.0 / rate)
+        if t > seconds:
+            break
+        n = int(rng.integers(0, len(nets)))
+        C = max(2, int(10 ** rng.uniform(2, np.log10(5000)) * scale))
+        st = make_stimulus(nets[n].netlist.num_inputs, C, seed * 100_000 + len(reqs), 200, 50)
+        r = dict(arrival=t, netlist=n, stim=st)
+        if rng.uniform() < 0.3:
+            G = nets[n].netlist.num_gates
+            r["edit_gate"] = rng.choice(G, size=max(1, G // 100), replace=False).astype(np.int32)
+            r["edit_delta"] = (rng.choice([-1, 1], size=r["edit_gate"].size) *
+                               rng.integers(10, 51, size=r["edit_gate"].size)).astype(np.int32)
+        reqs.append(r)
+    return nets, reqs

@@ -1,0 +1,294 @@
+/*
+ * gatspi.h -- C interface of a GB300 (sm_103a) gate-level re-simulator with
+ * the delay semantics of GATSPI (Zhang, Ren, Sridharan, Khailany, "GATSPI:
+ * GPU Accelerated Gate-Level Simulation for Power Improvement", DAC 2022).
+ *
+ * What it computes (Section 3, Algorithm 1): input waveforms of the primary
+ * and pseudo-primary inputs are given per clock cycle ("re-simulation",
+ * Section 1); every combinational gate's output waveform is derived level by
+ * level, in parallel over the gates of a level and over independent windows
+ * of cycles, with
+ *   - cell functions as truth tables Y[colInd], pin 1 = least significant
+ *     bit of colInd;
+ *   - per-pin interconnect delays [rise, fall] with inertial filtering of
+ *     pulses narrower than the delay of their first edge;
+ *   - multiple-simultaneous-input switching (all pins arriving at the same
+ *     time switch before the output is re-evaluated);
+ *   - gate delays read from the switching pin's table, indexed by its edge,
+ *     the output edge and the other pins' values (SDF COND);
+ *   - gate inertial filtering with PATHPULSEPERCENT = 100;
+ * and every net is reduced to SAIF figures T0 / T1 / TC (Section 3: the
+ * simulator produces SAIF files for power analysis).
+ *
+ * Conventions
+ *   - Nets 0..I-1 are inputs; gate g (0-based) drives net I+g.  Every fanin
+ *     net of gate g has a smaller id than I+g (this is how acyclicity is
+ *     checked).  Gates need not be sorted by level: the library levelizes.
+ *   - Pins of gate g are fanin_ptr[g] .. fanin_ptr[g+1]-1 (pin 1 first),
+ *     1 to 4 pins per gate.
+ *   - Times are int32 picoseconds.  A window of W cycles is simulated on its
+ *     own time axis [0, W*L) starting from the zero-delay settled values of
+ *     the inputs' values at the window start; edges that land after W*L are
+ *     kept and counted in TC, while T0/T1 integrate only over [0, W*L).
+ *   - Values are 0/1 (2-value simulation, Section 2).
+ *
+ * Ownership and errors
+ *   - Host arrays passed in are owned by the caller and copied before the
+ *     call returns.  The library owns all device memory it uses.
+ *   - Every call returns GATSPI_OK (0) or a negative status; the message of
+ *     the last failure is returned by gatspi_last_error().
+ *   - A context is bound to one CUDA device and is not thread-safe.
+ *   - Calls out of order (for example gatspi_simulate before a netlist, its
+ *     delays and a stimulus were loaded) return GATSPI_ESTATE.
+ */
+#ifndef GATSPI_H
+#define GATSPI_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GATSPI_OK 0
+#define GATSPI_EINVAL (-1)    /* bad argument (message says which) */
+#define GATSPI_ENOMEM (-2)    /* device or host allocation failed */
+#define GATSPI_ECAPACITY (-3) /* waveforms do not fit, even one window per batch */
+#define GATSPI_ECUDA (-4)     /* a CUDA call failed */
+#define GATSPI_ETIMEOUT (-5)  /* a bounded device-side wait ran out */
+#define GATSPI_ESTATE (-6)    /* call out of order */
+
+typedef struct gatspi_ctx gatspi_ctx;
+
+/* Options of one gatspi_simulate call.  Zero means "default" everywhere. */
+typedef struct gatspi_opts {
+  int32_t window_cycles; /* W: cycles per independent window (default 1) */
+  int32_t batch_windows; /* windows resident on the device at once; 0 = all
+                            that fit in the arena (halved on overflow) */
+  int32_t tile_items;    /* (gate, window) items per thread block: 128, 256
+                            or 512; 0 = 256 */
+  int32_t time_kernels;  /* 1 = time every propagation launch with CUDA
+                            events on the library's stream (read back with
+                            gatspi_get_stats) */
+  int32_t reserved[4];   /* must be 0 */
+} gatspi_opts;
+
+/* Figures of the last gatspi_simulate call. */
+typedef struct gatspi_stats {
+  double prop_ms;          /* summed propagation-kernel time (time_kernels) */
+  double input_ms;         /* summed input-restructuring kernel time */
+  double wall_ms;          /* host wall time of gatspi_simulate */
+  double device_ms;        /* device time from the first to the last kernel
+                              of the call, CUDA events (time_kernels) */
+  int64_t kernel_launches; /* kernels of this library launched */
+  int64_t prop_launches;   /* propagation-kernel launches */
+  int64_t items;           /* (gate, window) items simulated */
+  int64_t edges;           /* waveform edges stored, all nets and windows */
+  int64_t algo_bytes;      /* algorithmic bytes of the propagation kernels:
+                              per (gate, window) item, per fanin pin
+                              4 (offset) + 1 (start value) + 4 * edges read,
+                              plus 4 + 1 + 4 * edges written for the output */
+  int32_t batches;         /* device batches of windows */
+  int32_t windows;         /* windows simulated */
+  int32_t batch_windows;   /* windows per batch actually used */
+  int32_t levels;          /* logic depth D */
+} gatspi_stats;
+
+/*
+ * Create a context on CUDA device `device`.  `arena_bytes` caps the device
+ * memory used for waveforms (0 = 85% of the device memory free now).
+ * Errors: EINVAL (bad device), ECUDA.
+ */
+int gatspi_create(gatspi_ctx** out, int device, size_t arena_bytes);
+
+/* Free every device and host resource of the context (NULL is allowed). */
+int gatspi_destroy(gatspi_ctx* ctx);
+
+/* Message of the last failed call on this context ("" if none). */
+const char* gatspi_last_error(gatspi_ctx* ctx);
+
+/*
+ * Load the combinational netlist (Section 3: the netlist, its levelization
+ * and the cell truth tables of Fig. "WaveformLUTSDF").
+ *   num_inputs  I >= 1 primary/pseudo-primary inputs (nets 0..I-1)
+ *   num_gates   G >= 0
+ *   fanin_ptr   int32 [G+1], fanin_ptr[0] = 0, non-decreasing, 1..4 pins/gate
+ *   fanin_net   int32 [P = fanin_ptr[G]], fanin_net[p] < I + g for pins of g
+ *   lut         uint16 [G], bit k = output for column index k (pin 1 = bit 0)
+ * Replaces any previous netlist and drops loaded delays, stimulus and
+ * results.  Errors: EINVAL (pin count, net id or cycle), ENOMEM, ECUDA.
+ */
+int gatspi_load_netlist(gatspi_ctx* ctx, int32_t num_inputs, int32_t num_gates,
+                        const int32_t* fanin_ptr, const int32_t* fanin_net,
+                        const uint16_t* lut);
+
+/*
+ * Load (or replace, for a delay edit) the delays of the loaded netlist
+ * (Algorithm 1 inputs delta_i and d_i; SDF IOPATH / COND / INTERCONNECT).
+ *   gate_delay  int32 [P][2 inEdge][2 outEdge][8 side]: delay of an output
+ *               edge caused by pin p (1 = rising), with `side` the other
+ *               pins' values in pin order compressed to n-1 bits; columns
+ *               >= 2^(n-1) are ignored
+ *   wire_delay  int32 [P][2]: interconnect delay to pin p for a rising /
+ *               falling edge of the driving net
+ * All used entries must be >= 1 ps.  Errors: ESTATE (no netlist), EINVAL.
+ */
+int gatspi_load_delays(gatspi_ctx* ctx, const int32_t* gate_delay, const int32_t* wire_delay);
+
+/*
+ * Set (n_edits > 0) or clear (n_edits = 0) a delay edit on the loaded
+ * delays without reloading them: gate edit_gate[k] (caller numbering) has
+ * every gate delay shifted by edit_delta[k] ps, clamped at 1 ps -- the
+ * re-timing of a cell resize in a glitch-optimization loop (Section 4).
+ * The arrays are copied.  Errors: ESTATE (no delays), EINVAL.
+ */
+int gatspi_set_edit(gatspi_ctx* ctx, int32_t n_edits, const int32_t* edit_gate,
+                    const int32_t* edit_delta);
+
+/*
+ * Set the input stimulus: C cycles of L ps.
+ *   init       uint8 [I], value of each input at time 0 of cycle 0
+ *   edge_ptr   int64 [I*C+1], edges of input i in cycle c are
+ *              edge_time[edge_ptr[i*C+c] .. edge_ptr[i*C+c+1])
+ *   edge_time  int32, strictly increasing within each (i, c), in [0, L);
+ *              each edge toggles the input
+ * The stimulus is copied to the device once.  Errors: ESTATE (no netlist),
+ * EINVAL (ordering, range), ENOMEM, ECUDA.
+ */
+int gatspi_set_stimulus(gatspi_ctx* ctx, int32_t num_cycles, int32_t cycle_ps,
+                        const uint8_t* init, const int64_t* edge_ptr, const int32_t* edge_time);
+
+/*
+ * Simulate every window (Algorithm 1 for every gate and window, level by
+ * level; output storage sized by a scan over the produced edge counts,
+ * Section 3) and accumulate SAIF.  Synchronous.  `opts` may be NULL.
+ * Errors: ESTATE, EINVAL (options, or times that could overflow int32),
+ * ECAPACITY, ETIMEOUT, ECUDA.
+ */
+int gatspi_simulate(gatspi_ctx* ctx, const gatspi_opts* opts);
+
+/*
+ * SAIF of the last simulation, per net in the caller's net numbering:
+ *   t0, t1  int64 [I+G], time at 0 / 1 in ps summed over windows
+ *   tc      int64 [I+G], number of edges (toggle count)
+ * Any pointer may be NULL.  Errors: ESTATE (nothing simulated).
+ */
+int gatspi_saif(gatspi_ctx* ctx, int64_t* t0, int64_t* t1, int64_t* tc);
+
+/*
+ * Waveforms of every net in window `window` of the last simulation.  Only
+ * windows of the last device batch are resident (all windows when they fit
+ * in one batch); others return ESTATE.
+ *   init   uint8 [I+G]  value at the window start
+ *   ptr    int64 [I+G+1] edges of net n are times[ptr[n] .. ptr[n+1])
+ *   times  int32 [cap]   window-relative edge times; may be NULL to size it
+ *   total  out: number of edges (ptr[I+G])
+ * Returns ECAPACITY if cap < total (init and ptr are still filled).
+ */
+int gatspi_read_window(gatspi_ctx* ctx, int32_t window, uint8_t* init, int64_t* ptr,
+                       int32_t* times, int64_t cap, int64_t* total);
+
+/* Figures of the last gatspi_simulate call.  Errors: EINVAL (NULL). */
+int gatspi_get_stats(gatspi_ctx* ctx, gatspi_stats* out);
+
+
+/* ------------------------------------------------------------------------
+ * Multi-job engine: batched and served re-simulation.
+ *
+ * Many jobs (netlist + stimulus + optional delay edit) run together: each
+ * job is cut into parts (windows), parts are admitted while their waveform
+ * store fits in the engine's device-memory budget, and every step launches
+ * one propagation kernel covering the next logic level of every admitted
+ * part, whatever its netlist or level (continuous batching).  A part that
+ * finishes frees its memory at once, so waiting parts join mid-flight.
+ * Each part's results are bit-identical to a plain gatspi_simulate of the
+ * same job: parts never share look-back chains or waveform stores.
+ * The paper runs one design at a time (Section 3); its glitch-optimization
+ * loop (Section 4) re-simulates after delay edits, which is the workload
+ * the edits below serve.
+ * ---------------------------------------------------------------------- */
+typedef struct gatspi_engine gatspi_engine;
+
+typedef struct gatspi_engine_opts {
+  int32_t tile_items;  /* items per block for every launch: 128, 256, 512;
+                          0 = 256 */
+  int32_t max_active;  /* parts in flight at once; 0 = 1024 */
+  int64_t part_items;  /* max (gate, window) items of one part; 0 = 2^28 */
+  int32_t reserved[4]; /* must be 0 */
+} gatspi_engine_opts;
+
+typedef struct gatspi_engine_stats {
+  int64_t steps;          /* propagation launches (one per step) */
+  int64_t kernel_launches;
+  int64_t parts_done;
+  int64_t parts_retried;  /* parts re-run with a larger waveform store */
+  int64_t items;          /* (gate, window) items simulated */
+  int64_t bytes_peak;     /* largest device bytes held by admitted parts */
+  int32_t active;         /* parts in flight now */
+  int32_t queued;         /* parts waiting for admission now */
+} gatspi_engine_stats;
+
+/* Job states reported by gatspi_engine_poll. */
+#define GATSPI_JOB_QUEUED 0
+#define GATSPI_JOB_RUNNING 1
+#define GATSPI_JOB_DONE 2
+#define GATSPI_JOB_FAILED 3
+
+/* Create an engine on `device` holding at most `arena_bytes` of waveform
+ * stores (0 = 85% of free memory).  `opts` may be NULL.
+ * Errors: EINVAL, ECUDA. */
+int gatspi_engine_create(gatspi_engine** out, int device, size_t arena_bytes,
+                         const gatspi_engine_opts* opts);
+
+/* Wait for the device, then free everything (NULL is allowed). */
+int gatspi_engine_destroy(gatspi_engine* eng);
+
+const char* gatspi_engine_last_error(gatspi_engine* eng);
+
+/* Make a netlist and its delays resident (same arrays and rules as
+ * gatspi_load_netlist + gatspi_load_delays); *netlist_id receives its id.
+ * Errors: EINVAL, ENOMEM, ECUDA. */
+int gatspi_engine_add_netlist(gatspi_engine* eng, int32_t num_inputs, int32_t num_gates,
+                              const int32_t* fanin_ptr, const int32_t* fanin_net,
+                              const uint16_t* lut, const int32_t* gate_delay,
+                              const int32_t* wire_delay, int32_t* netlist_id);
+
+/* Queue a job on a resident netlist: a stimulus (same arrays and rules as
+ * gatspi_set_stimulus, copied before return), windows of window_cycles
+ * cycles (0 = 1), and an optional delay edit scoped to this job: gate
+ * edit_gate[k] (caller numbering) has every gate delay shifted by
+ * edit_delta[k] ps, clamped at 1 ps (a cell-resize step of a
+ * glitch-optimization loop).  *job_id receives the job's id.
+ * Errors: EINVAL (ids, stimulus, edits), ENOMEM, ECUDA. */
+int gatspi_engine_submit(gatspi_engine* eng, int32_t netlist_id, int32_t num_cycles,
+                         int32_t cycle_ps, const uint8_t* init, const int64_t* edge_ptr,
+                         const int32_t* edge_time, int32_t window_cycles, int32_t n_edits,
+                         const int32_t* edit_gate, const int32_t* edit_delta, int64_t* job_id);
+
+/* One engine step: retire finished parts, admit queued parts that fit, and
+ * launch one level of every admitted part.  Returns without waiting for the
+ * device except when a retired part's status must be read.  *active and
+ * *queued (may be NULL) receive the parts in flight and waiting.
+ * Errors: ETIMEOUT, ECAPACITY (a part cannot fit even alone), ECUDA. */
+int gatspi_engine_step(gatspi_engine* eng, int32_t* active, int32_t* queued);
+
+/* Step until every queued job is done. */
+int gatspi_engine_drain(gatspi_engine* eng);
+
+/* State of a job, and its SAIF when done (t0, t1, tc: int64 [I+G] in the
+ * caller's net numbering; any may be NULL).  Errors: EINVAL (unknown id). */
+int gatspi_engine_poll(gatspi_engine* eng, int64_t job_id, int32_t* state, int64_t* t0,
+                       int64_t* t1, int64_t* tc);
+
+/* Forget a finished job and free its device memory.  Errors: EINVAL,
+ * ESTATE (job not finished). */
+int gatspi_engine_release(gatspi_engine* eng, int64_t job_id);
+
+int gatspi_engine_get_stats(gatspi_engine* eng, gatspi_engine_stats* out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GATSPI_H */

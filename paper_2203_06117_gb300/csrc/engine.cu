@@ -1,0 +1,758 @@
+// Multi-job engine (include/gatspi.h, "Multi-job engine"): resident
+// netlists, a queue of jobs cut into window parts, admission by device
+// memory, and steps that launch one propagation kernel over the next level
+// of every admitted part (continuous batching across jobs, netlists and
+// levels).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "gatspi.h"
+#include "host_common.h"
+#include "kernels.cuh"
+
+using namespace gatspi_dev;
+
+namespace {
+
+constexpr int64_t kAlign = 256;
+int64_t align_up(int64_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+struct ENetlist {
+  gatspi_host::Prepared r;
+  int32_t max_gate = 0, max_wire = 0;
+  int32_t* d_fanin_ptr = nullptr;
+  int32_t* d_fanin_net = nullptr;
+  int32_t* d_net_level = nullptr;
+  int32_t* d_gate_delay = nullptr;
+  int32_t* d_wire_delay = nullptr;
+  uint16_t* d_lut = nullptr;
+  double edges_per_item = 2.0;  // observed edges per (net, window), sizes new parts
+};
+
+struct EJob {
+  int64_t id = 0;
+  int32_t net = 0, C = 0, L = 0, W = 1, n_windows = 0, max_edit = 0;
+  std::vector<int64_t> edge_ptr;
+  int64_t* d_edge_ptr = nullptr;
+  int32_t* d_edge_time = nullptr;
+  uint8_t* d_init_in = nullptr;
+  int32_t* d_gate_delta = nullptr;
+  unsigned long long* d_t1 = nullptr;
+  unsigned long long* d_tc = nullptr;
+  int32_t parts_total = 0, parts_done = 0;
+  int state = GATSPI_JOB_QUEUED;
+  std::string err;
+  cudaEvent_t done_ev = nullptr;
+  bool done_recorded = false;
+};
+
+struct PartResult {
+  int32_t status;
+  int32_t pad;
+  long long edges;
+};
+
+struct EPart {
+  int64_t job = 0;
+  int32_t w0 = 0, nw = 0, level = 0, D = 0;
+  int64_t edge_hint = 0;
+  char* mem = nullptr;
+  size_t bytes = 0;
+  uint8_t* init = nullptr;
+  int32_t* off = nullptr;
+  int32_t* times = nullptr;
+  long long cap = 0;
+  long long* lvl_base = nullptr;
+  unsigned long long* tiles = nullptr;
+  int32_t* status = nullptr;
+  unsigned long long* t1 = nullptr;
+  unsigned long long* tc = nullptr;
+  size_t zero_off = 0, zero_bytes = 0;
+  std::vector<int64_t> tile_base;
+  int32_t slot = -1;  // pinned result slot
+  cudaEvent_t ev = nullptr;
+};
+
+}  // namespace
+
+struct gatspi_engine {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  std::string err;
+  size_t budget = 0, in_use = 0;
+  gatspi_engine_opts opts{};
+  int tile = 256;
+  std::vector<std::unique_ptr<ENetlist>> nets;
+  std::map<int64_t, std::unique_ptr<EJob>> jobs;
+  int64_t next_job = 1;
+  std::deque<std::unique_ptr<EPart>> queued;
+  std::vector<std::unique_ptr<EPart>> active;
+  std::vector<std::unique_ptr<EPart>> finishing;
+  // per-step staging: pinned host ring -> one device buffer
+  static constexpr int kRing = 4;
+  char* h_stage[kRing] = {};
+  cudaEvent_t stage_ev[kRing] = {};
+  size_t h_stage_cap = 0;
+  int ring = 0;
+  char* d_stage = nullptr;
+  size_t d_stage_cap = 0;
+  int32_t* d_counter = nullptr;
+  // pinned per-part result slots
+  PartResult* h_results = nullptr;
+  std::vector<int32_t> free_slots;
+  std::vector<cudaEvent_t> free_events;
+  gatspi_engine_stats stats{};
+};
+
+namespace {
+
+int efail(gatspi_engine* e, int code, const std::string& msg) {
+  if (e) e->err = msg;
+  return code;
+}
+
+#define ECK(call)                                                                        \
+  do {                                                                                   \
+    cudaError_t e_ = (call);                                                             \
+    if (e_ != cudaSuccess)                                                               \
+      return efail(eng, GATSPI_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+template <class T>
+void dfree(T*& p) {
+  if (p) cudaFree(p);
+  p = nullptr;
+}
+
+template <class T>
+int eupload(gatspi_engine* eng, T*& dst, const T* src, size_t n) {
+  dfree(dst);
+  ECK(cudaMalloc(&dst, std::max<size_t>(n, 1) * sizeof(T)));
+  if (src && n) ECK(cudaMemcpy(dst, src, n * sizeof(T), cudaMemcpyHostToDevice));
+  return GATSPI_OK;
+}
+
+// Stream-ordered allocation and copy (the host buffer may be reused as soon
+// as this returns: pageable copies are staged before the call returns).
+template <class T>
+int eupload_async(gatspi_engine* eng, T*& dst, const T* src, size_t n) {
+  ECK(cudaMallocAsync((void**)&dst, std::max<size_t>(n, 1) * sizeof(T), eng->stream));
+  if (src && n) ECK(cudaMemcpyAsync(dst, src, n * sizeof(T), cudaMemcpyHostToDevice, eng->stream));
+  return GATSPI_OK;
+}
+
+template <class T>
+void dfree_async(T*& p, cudaStream_t s) {
+  if (p) cudaFreeAsync(p, s);
+  p = nullptr;
+}
+
+// Lay out one part's device memory; returns the total bytes.
+size_t part_layout(const ENetlist& nl, EPart& p, int tile, char* base) {
+  const int64_t N = nl.r.N, D = nl.r.D, NW = p.nw;
+  int64_t o = 0;
+  const int64_t o_init = o; o = align_up(o + N * NW);
+  const int64_t o_off = o; o = align_up(o + (N * NW + D + 2) * 4);
+  const int64_t o_lvl = o; o = align_up(o + (D + 2) * 8);
+  // zeroed region: look-back words, status, part SAIF
+  const int64_t o_zero = o;
+  p.tile_base.assign(D + 2, 0);
+  int64_t tiles = 0;
+  for (int32_t l = 1; l <= D; ++l) {
+    p.tile_base[l] = tiles;
+    const int64_t items = (int64_t)(nl.r.lvl_gate_begin[l + 1] - nl.r.lvl_gate_begin[l]) * NW;
+    tiles += (items + tile - 1) / tile;
+  }
+  const int64_t o_tiles = o; o = align_up(o + tiles * 8);
+  const int64_t o_status = o; o = align_up(o + 8);
+  const int64_t o_t1 = o; o = align_up(o + N * 8);
+  const int64_t o_tc = o; o = align_up(o + N * 8);
+  const int64_t zero_end = o;
+  const int64_t o_times = o; o = align_up(o + p.edge_hint * 4);
+  if (base) {
+    p.init = (uint8_t*)(base + o_init);
+    p.off = (int32_t*)(base + o_off);
+    p.lvl_base = (long long*)(base + o_lvl);
+    p.tiles = (unsigned long long*)(base + o_tiles);
+    p.status = (int32_t*)(base + o_status);
+    p.t1 = (unsigned long long*)(base + o_t1);
+    p.tc = (unsigned long long*)(base + o_tc);
+    p.times = (int32_t*)(base + o_times);
+    p.cap = p.edge_hint;
+    p.zero_off = (size_t)o_zero;
+    p.zero_bytes = (size_t)(zero_end - o_zero);
+  }
+  return (size_t)o;
+}
+
+JobView make_view(const ENetlist& nl, const EJob& j, const EPart& p) {
+  JobView v{};
+  v.fanin_ptr = nl.d_fanin_ptr; v.fanin_net = nl.d_fanin_net; v.lut = nl.d_lut;
+  v.gate_delay = nl.d_gate_delay; v.wire_delay = nl.d_wire_delay; v.net_level = nl.d_net_level;
+  v.gate_delta = j.d_gate_delta;
+  v.init = p.init; v.off = p.off; v.times = p.times; v.lvl_base = p.lvl_base; v.capacity = p.cap;
+  v.saif_t1 = p.t1; v.saif_tc = p.tc; v.status = p.status;
+  v.I = nl.r.I; v.NW = p.nw; v.w0 = p.w0; v.W = j.W; v.C = j.C; v.L = j.L;
+  return v;
+}
+
+void free_job_device(EJob& j, cudaStream_t s) {
+  dfree_async(j.d_edge_ptr, s); dfree_async(j.d_edge_time, s); dfree_async(j.d_init_in, s);
+  dfree_async(j.d_gate_delta, s); dfree_async(j.d_t1, s); dfree_async(j.d_tc, s);
+  if (j.done_ev) cudaEventDestroy(j.done_ev);
+  j.done_ev = nullptr;
+}
+
+int fail_job(gatspi_engine* eng, EJob& j, int code, const std::string& why) {
+  j.state = GATSPI_JOB_FAILED;
+  j.err = why;
+  // drop its queued parts
+  std::deque<std::unique_ptr<EPart>> keep;
+  for (auto& p : eng->queued)
+    if (p->job != j.id) keep.push_back(std::move(p));
+  eng->queued.swap(keep);
+  return efail(eng, code, "job " + std::to_string(j.id) + ": " + why);
+}
+
+int stage_reserve(gatspi_engine* eng, size_t bytes) {
+  if (bytes > eng->h_stage_cap) {
+    ECK(cudaStreamSynchronize(eng->stream));
+    size_t cap = std::max<size_t>(bytes, 2 * eng->h_stage_cap);
+    for (int k = 0; k < gatspi_engine::kRing; ++k) {
+      if (eng->h_stage[k]) cudaFreeHost(eng->h_stage[k]);
+      eng->h_stage[k] = nullptr;
+      ECK(cudaMallocHost(&eng->h_stage[k], cap));
+    }
+    dfree(eng->d_stage);
+    ECK(cudaMalloc(&eng->d_stage, cap));
+    eng->h_stage_cap = eng->d_stage_cap = cap;
+  }
+  return GATSPI_OK;
+}
+
+// Retire parts whose last level has finished on the device.
+int retire(gatspi_engine* eng, bool wait_one) {
+  bool waited = false;
+  for (size_t k = 0; k < eng->finishing.size();) {
+    EPart& p = *eng->finishing[k];
+    cudaError_t q = cudaEventQuery(p.ev);
+    if (q == cudaErrorNotReady && wait_one && !waited) {
+      ECK(cudaEventSynchronize(p.ev));
+      waited = true;
+      q = cudaSuccess;
+    }
+    if (q == cudaErrorNotReady) {
+      ++k;
+      continue;
+    }
+    if (q != cudaSuccess) return efail(eng, GATSPI_ECUDA, std::string("part event: ") + cudaGetErrorString(q));
+    const PartResult res = eng->h_results[p.slot];
+    EJob& j = *eng->jobs.at(p.job);
+    ENetlist& nl = *eng->nets[j.net];
+    std::unique_ptr<EPart> own = std::move(eng->finishing[k]);
+    eng->finishing.erase(eng->finishing.begin() + (long)k);
+    eng->free_slots.push_back(p.slot);
+    eng->free_events.push_back(p.ev);
+    p.ev = nullptr;
+    int rc = GATSPI_OK;
+    if (j.state == GATSPI_JOB_FAILED) {
+      // job already failed: just drop the part
+    } else if (res.status & kStTimeout) {
+      rc = fail_job(eng, j, GATSPI_ETIMEOUT, "a device-side wait ran out");
+    } else if (res.status & (kStCapacity | kStOffset | kStCorrupt)) {
+      eng->stats.parts_retried++;
+      std::unique_ptr<EPart> again(new EPart());
+      again->job = p.job;
+      again->D = p.D;
+      if ((res.status & kStOffset) && p.nw > 1) {
+        // a level overflowed int32 offsets: split the windows
+        std::unique_ptr<EPart> b(new EPart());
+        const int32_t h = p.nw / 2;
+        again->w0 = p.w0; again->nw = h; again->edge_hint = p.edge_hint / 2;
+        b->job = p.job; b->D = p.D; b->w0 = p.w0 + h; b->nw = p.nw - h; b->edge_hint = p.edge_hint / 2;
+        j.parts_total++;
+        eng->queued.push_front(std::move(b));
+      } else if (res.status & kStOffset) {
+        rc = fail_job(eng, j, GATSPI_ECAPACITY, "one window's edges exceed the int32 offset range");
+      } else {
+        again->w0 = p.w0; again->nw = p.nw;
+        again->edge_hint = std::max<int64_t>(2 * p.edge_hint, res.edges + 1024);
+      }
+      if (j.state != GATSPI_JOB_FAILED) eng->queued.push_front(std::move(again));
+    } else {
+      const int32_t N = nl.r.N;
+      saif_add_kernel<<<(N + 255) / 256, 256, 0, eng->stream>>>(N, p.t1, p.tc, j.d_t1, j.d_tc);
+      eng->stats.kernel_launches++;
+      const double obs = (double)res.edges / ((double)N * p.nw);
+      nl.edges_per_item = std::max(nl.edges_per_item * 0.98, obs * 1.1);
+      j.parts_done++;
+      eng->stats.parts_done++;
+      if (j.parts_done == j.parts_total) {
+        if (!j.done_ev) ECK(cudaEventCreateWithFlags(&j.done_ev, cudaEventDisableTiming));
+        ECK(cudaEventRecord(j.done_ev, eng->stream));
+        j.done_recorded = true;
+      }
+    }
+    ECK(cudaFreeAsync(p.mem, eng->stream));
+    eng->in_use -= p.bytes;
+    if (rc) return rc;
+  }
+  return GATSPI_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int gatspi_engine_create(gatspi_engine** out, int device, size_t arena_bytes, const gatspi_engine_opts* opts) {
+  if (!out) return GATSPI_EINVAL;
+  *out = nullptr;
+  int n = 0;
+  if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) {
+    cudaGetLastError();
+    return GATSPI_EINVAL;
+  }
+  gatspi_engine_opts o{};
+  if (opts) o = *opts;
+  for (int k = 0; k < 4; ++k)
+    if (o.reserved[k]) return GATSPI_EINVAL;
+  const int tile = o.tile_items ? o.tile_items : 256;
+  if (tile != 128 && tile != 256 && tile != 512) return GATSPI_EINVAL;
+  if (o.max_active < 0 || o.part_items < 0) return GATSPI_EINVAL;
+  auto* eng = new gatspi_engine();
+  eng->device = device;
+  eng->opts = o;
+  eng->tile = tile;
+  if (!eng->opts.max_active) eng->opts.max_active = 1024;
+  if (!eng->opts.part_items) eng->opts.part_items = 1ll << 28;
+  if (cudaSetDevice(device) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&eng->stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaMalloc(&eng->d_counter, sizeof(int32_t)) != cudaSuccess ||
+      cudaMallocHost(&eng->h_results, sizeof(PartResult) * (size_t)eng->opts.max_active) != cudaSuccess) {
+    cudaGetLastError();
+    gatspi_engine_destroy(eng);
+    return GATSPI_ECUDA;
+  }
+  for (int k = 0; k < gatspi_engine::kRing; ++k)
+    if (cudaEventCreateWithFlags(&eng->stage_ev[k], cudaEventDisableTiming) != cudaSuccess) {
+      gatspi_engine_destroy(eng);
+      return GATSPI_ECUDA;
+    }
+  for (int32_t s = eng->opts.max_active - 1; s >= 0; --s) eng->free_slots.push_back(s);
+  // keep freed part memory in the device pool between steps
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
+    uint64_t thr = ~0ull;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+  }
+  size_t free_b = 0, total_b = 0;
+  cudaMemGetInfo(&free_b, &total_b);
+  eng->budget = arena_bytes ? arena_bytes : (size_t)(0.85 * (double)free_b);
+  *out = eng;
+  return GATSPI_OK;
+}
+
+int gatspi_engine_destroy(gatspi_engine* eng) {
+  if (!eng) return GATSPI_OK;
+  cudaSetDevice(eng->device);
+  if (eng->stream) cudaStreamSynchronize(eng->stream);
+  auto drop = [&](std::unique_ptr<EPart>& p) {
+    if (p->mem) cudaFree(p->mem);
+    if (p->ev) cudaEventDestroy(p->ev);
+  };
+  for (auto& p : eng->active) drop(p);
+  for (auto& p : eng->finishing) drop(p);
+  for (auto& kv : eng->jobs) free_job_device(*kv.second, eng->stream);
+  if (eng->stream) cudaStreamSynchronize(eng->stream);
+  for (auto& nl : eng->nets) {
+    dfree(nl->d_fanin_ptr); dfree(nl->d_fanin_net); dfree(nl->d_net_level);
+    dfree(nl->d_gate_delay); dfree(nl->d_wire_delay); dfree(nl->d_lut);
+  }
+  for (int k = 0; k < gatspi_engine::kRing; ++k) {
+    if (eng->h_stage[k]) cudaFreeHost(eng->h_stage[k]);
+    if (eng->stage_ev[k]) cudaEventDestroy(eng->stage_ev[k]);
+  }
+  for (auto e : eng->free_events) cudaEventDestroy(e);
+  dfree(eng->d_stage);
+  dfree(eng->d_counter);
+  if (eng->h_results) cudaFreeHost(eng->h_results);
+  if (eng->stream) cudaStreamDestroy(eng->stream);
+  // hand the memory parked in the stream-ordered pool back to the device
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, eng->device) == cudaSuccess) cudaMemPoolTrimTo(pool, 0);
+  delete eng;
+  return GATSPI_OK;
+}
+
+const char* gatspi_engine_last_error(gatspi_engine* eng) { return eng ? eng->err.c_str() : "null engine"; }
+
+int gatspi_engine_add_netlist(gatspi_engine* eng, int32_t num_inputs, int32_t num_gates,
+                              const int32_t* fanin_ptr, const int32_t* fanin_net, const uint16_t* lut,
+                              const int32_t* gate_delay, const int32_t* wire_delay, int32_t* netlist_id) {
+  if (!eng || !netlist_id) return GATSPI_EINVAL;
+  std::unique_ptr<ENetlist> nl(new ENetlist());
+  std::string why = gatspi_host::prepare_netlist(num_inputs, num_gates, fanin_ptr, fanin_net, lut, &nl->r);
+  if (!why.empty()) return efail(eng, GATSPI_EINVAL, why);
+  std::vector<int32_t> gd, wd;
+  why = gatspi_host::prepare_delays(nl->r, gate_delay, wire_delay, &gd, &wd, &nl->max_gate, &nl->max_wire);
+  if (!why.empty()) return efail(eng, GATSPI_EINVAL, why);
+  ECK(cudaSetDevice(eng->device));
+  int rc;
+  if ((rc = eupload(eng, nl->d_fanin_ptr, nl->r.fanin_ptr.data(), nl->r.fanin_ptr.size()))) return rc;
+  if ((rc = eupload(eng, nl->d_fanin_net, nl->r.fanin_net.data(), nl->r.fanin_net.size()))) return rc;
+  if ((rc = eupload(eng, nl->d_net_level, nl->r.net_level.data(), nl->r.net_level.size()))) return rc;
+  if ((rc = eupload(eng, nl->d_lut, nl->r.lut.data(), nl->r.lut.size()))) return rc;
+  if ((rc = eupload(eng, nl->d_gate_delay, gd.data(), gd.size()))) return rc;
+  if ((rc = eupload(eng, nl->d_wire_delay, wd.data(), wd.size()))) return rc;
+  *netlist_id = (int32_t)eng->nets.size();
+  eng->nets.push_back(std::move(nl));
+  return GATSPI_OK;
+}
+
+int gatspi_engine_submit(gatspi_engine* eng, int32_t netlist_id, int32_t num_cycles, int32_t cycle_ps,
+                         const uint8_t* init, const int64_t* edge_ptr, const int32_t* edge_time,
+                         int32_t window_cycles, int32_t n_edits, const int32_t* edit_gate,
+                         const int32_t* edit_delta, int64_t* job_id) {
+  if (!eng || !job_id) return GATSPI_EINVAL;
+  if (netlist_id < 0 || netlist_id >= (int32_t)eng->nets.size())
+    return efail(eng, GATSPI_EINVAL, "unknown netlist id");
+  ENetlist& nl = *eng->nets[netlist_id];
+  std::string why = gatspi_host::validate_stimulus(nl.r.I, num_cycles, cycle_ps, init, edge_ptr, edge_time);
+  if (!why.empty()) return efail(eng, GATSPI_EINVAL, why);
+  const int32_t W = window_cycles ? window_cycles : 1;
+  if (W < 1) return efail(eng, GATSPI_EINVAL, "window_cycles must be >= 1");
+  if (n_edits < 0 || (n_edits > 0 && (!edit_gate || !edit_delta)))
+    return efail(eng, GATSPI_EINVAL, "bad delay edit arrays");
+  std::vector<int32_t> delta;
+  int32_t max_edit = 0;
+  if (n_edits > 0) {
+    delta.assign(nl.r.G, 0);
+    for (int32_t k = 0; k < n_edits; ++k) {
+      const int32_t g = edit_gate[k];
+      if (g < 0 || g >= nl.r.G) return efail(eng, GATSPI_EINVAL, "edit names an unknown gate");
+      if (edit_delta[k] < -gatspi_host::kMaxDelay || edit_delta[k] > gatspi_host::kMaxDelay)
+        return efail(eng, GATSPI_EINVAL, "edit delta outside +-2^24 ps");
+      delta[nl.r.gate_int[g]] = edit_delta[k];
+      max_edit = std::max(max_edit, edit_delta[k]);
+    }
+  }
+  if (!gatspi_host::horizon_fits(W, num_cycles, cycle_ps, nl.r.D, nl.max_gate, nl.max_wire, max_edit))
+    return efail(eng, GATSPI_EINVAL, "window length plus path delays could overflow int32 ps");
+  ECK(cudaSetDevice(eng->device));
+  std::unique_ptr<EJob> j(new EJob());
+  j->id = eng->next_job++;
+  j->net = netlist_id;
+  j->C = num_cycles; j->L = cycle_ps; j->W = W; j->max_edit = max_edit;
+  j->n_windows = (num_cycles + W - 1) / W;
+  const int64_t n = (int64_t)nl.r.I * num_cycles;
+  j->edge_ptr.assign(edge_ptr, edge_ptr + n + 1);
+  int rc;
+  auto undo = [&](int code) { free_job_device(*j, eng->stream); return code; };
+  if ((rc = eupload_async(eng, j->d_edge_ptr, edge_ptr, (size_t)n + 1))) return undo(rc);
+  if ((rc = eupload_async(eng, j->d_edge_time, edge_time, (size_t)edge_ptr[n]))) return undo(rc);
+  if ((rc = eupload_async(eng, j->d_init_in, init, (size_t)nl.r.I))) return undo(rc);
+  if (n_edits > 0 && (rc = eupload_async(eng, j->d_gate_delta, delta.data(), delta.size()))) return undo(rc);
+  if ((rc = eupload_async<unsigned long long>(eng, j->d_t1, nullptr, nl.r.N))) return undo(rc);
+  if ((rc = eupload_async<unsigned long long>(eng, j->d_tc, nullptr, nl.r.N))) return undo(rc);
+  ECK(cudaMemsetAsync(j->d_t1, 0, sizeof(unsigned long long) * nl.r.N, eng->stream));
+  ECK(cudaMemsetAsync(j->d_tc, 0, sizeof(unsigned long long) * nl.r.N, eng->stream));
+  // cut into parts of at most part_items (gate, window) items and a level
+  // item count that fits int32
+  int64_t widest = nl.r.I;
+  for (int32_t l = 1; l <= nl.r.D; ++l)
+    widest = std::max<int64_t>(widest, nl.r.lvl_gate_begin[l + 1] - nl.r.lvl_gate_begin[l]);
+  int64_t per = std::max<int64_t>(1, eng->opts.part_items / std::max<int64_t>(nl.r.N, 1));
+  per = std::min<int64_t>(per, 0x7ffffff0ll / widest);
+  per = std::max<int64_t>(per, 1);
+  for (int32_t w0 = 0; w0 < j->n_windows; w0 += (int32_t)per) {
+    std::unique_ptr<EPart> p(new EPart());
+    p->job = j->id;
+    p->D = nl.r.D;
+    p->w0 = w0;
+    p->nw = (int32_t)std::min<int64_t>(per, j->n_windows - w0);
+    eng->queued.push_back(std::move(p));
+    j->parts_total++;
+  }
+  *job_id = j->id;
+  eng->jobs[j->id] = std::move(j);
+  return GATSPI_OK;
+}
+
+int gatspi_engine_step(gatspi_engine* eng, int32_t* active_out, int32_t* queued_out) {
+  if (!eng) return GATSPI_EINVAL;
+  ECK(cudaSetDevice(eng->device));
+  // 1. retire (block on the oldest finishing part only if nothing else can move)
+  const bool stuck = eng->active.empty() && !eng->finishing.empty();
+  int rc = retire(eng, stuck);
+  if (rc) return rc;
+
+  // 2. admit
+  std::vector<EPart*> admitted;
+  std::vector<std::vector<long long>> prefixes;
+  while (!eng->queued.empty() &&
+         (int32_t)(eng->active.size() + eng->finishing.size()) < eng->opts.max_active) {
+    EPart& p = *eng->queued.front();
+    EJob& j = *eng->jobs.at(p.job);
+    if (j.state == GATSPI_JOB_FAILED) {
+      eng->queued.pop_front();
+      continue;
+    }
+    ENetlist& nl = *eng->nets[j.net];
+    if (!p.edge_hint) {
+      // level-0 edges are known; the rest follows the netlist's history
+      const int32_t c0 = p.w0 * j.W, c1 = std::min((p.w0 + p.nw) * j.W, j.C);
+      int64_t l0 = 0;
+      for (int32_t i = 0; i < nl.r.I; ++i)
+        l0 += j.edge_ptr[(size_t)i * j.C + c1] - j.edge_ptr[(size_t)i * j.C + c0];
+      p.edge_hint = l0 + (int64_t)(nl.edges_per_item * (double)nl.r.G * p.nw * 1.25) + 4096;
+    }
+    const size_t bytes = part_layout(nl, p, eng->tile, nullptr);
+    if (bytes > eng->budget) {
+      if (p.nw > 1) {  // split and retry
+        std::unique_ptr<EPart> b(new EPart());
+        const int32_t h = p.nw / 2;
+        b->job = p.job; b->D = p.D; b->w0 = p.w0 + h; b->nw = p.nw - h;
+        p.nw = h;
+        p.edge_hint = 0;
+        j.parts_total++;
+        eng->queued.insert(eng->queued.begin() + 1, std::move(b));
+        continue;
+      }
+      return fail_job(eng, j, GATSPI_ECAPACITY, "one window does not fit in the engine's memory budget");
+    }
+    if (eng->in_use + bytes > eng->budget) break;
+    void* mem = nullptr;
+    if (cudaMallocAsync(&mem, bytes, eng->stream) != cudaSuccess) {
+      cudaGetLastError();
+      break;
+    }
+    std::unique_ptr<EPart> own = std::move(eng->queued.front());
+    eng->queued.pop_front();
+    own->mem = (char*)mem;
+    own->bytes = bytes;
+    part_layout(nl, *own, eng->tile, own->mem);
+    eng->in_use += bytes;
+    eng->stats.bytes_peak = std::max<int64_t>(eng->stats.bytes_peak, (int64_t)eng->in_use);
+    ECK(cudaMemsetAsync(own->mem + own->zero_off, 0, own->zero_bytes, eng->stream));
+    std::vector<long long> pre(nl.r.I);
+    long long l0 = 0;
+    const int32_t c0 = own->w0 * j.W, c1 = std::min((own->w0 + own->nw) * j.W, j.C);
+    for (int32_t i = 0; i < nl.r.I; ++i) {
+      pre[i] = l0;
+      l0 += j.edge_ptr[(size_t)i * j.C + c1] - j.edge_ptr[(size_t)i * j.C + c0];
+    }
+    prefixes.push_back(std::move(pre));
+    own->level = 0;
+    admitted.push_back(own.get());
+    eng->active.push_back(std::move(own));
+  }
+
+  // 3. stage: input prefixes of admitted parts, then the launch tables
+  std::vector<size_t> pre_off(admitted.size());
+  size_t bytes = 0;
+  for (size_t k = 0; k < admitted.size(); ++k) {
+    pre_off[k] = bytes;
+    bytes = (size_t)align_up((int64_t)(bytes + prefixes[k].size() * sizeof(long long)));
+  }
+  std::vector<EPart*> stepping;
+  for (auto& p : eng->active)
+    if (p->level >= 1 || std::find(admitted.begin(), admitted.end(), p.get()) != admitted.end())
+      stepping.push_back(p.get());
+  const size_t jobs_off = bytes;
+  bytes = (size_t)align_up((int64_t)(bytes + stepping.size() * sizeof(JobView)));
+  const size_t segs_off = bytes;
+  bytes = (size_t)align_up((int64_t)(bytes + stepping.size() * sizeof(MultiSeg)));
+  if ((rc = stage_reserve(eng, std::max<size_t>(bytes, 4096)))) return rc;
+  const int slot = eng->ring;
+  eng->ring = (eng->ring + 1) % gatspi_engine::kRing;
+  ECK(cudaEventSynchronize(eng->stage_ev[slot]));
+  char* h = eng->h_stage[slot];
+  for (size_t k = 0; k < admitted.size(); ++k)
+    std::memcpy(h + pre_off[k], prefixes[k].data(), prefixes[k].size() * sizeof(long long));
+  // levels: admitted parts run level 0 (inputs kernel) in this step and
+  // level 1 onwards from the next step
+  std::vector<JobView> views;
+  std::vector<MultiSeg> segs;
+  int64_t tiles = 0;
+  for (EPart* p : stepping) {
+    if (p->level < 1) continue;
+    EJob& j = *eng->jobs.at(p->job);
+    ENetlist& nl = *eng->nets[j.net];
+    const int32_t l = p->level;
+    MultiSeg s{};
+    s.seg.tile_state = p->tiles + p->tile_base[l];
+    s.seg.level = l;
+    s.seg.gate_begin = nl.r.lvl_gate_begin[l];
+    s.seg.net_end = nl.r.I + nl.r.lvl_gate_begin[l + 1];
+    s.seg.n_items = (nl.r.lvl_gate_begin[l + 1] - nl.r.lvl_gate_begin[l]) * p->nw;
+    s.seg.n_tiles = (s.seg.n_items + eng->tile - 1) / eng->tile;
+    s.job = (int32_t)views.size();
+    s.tile_begin = (int32_t)tiles;
+    tiles += s.seg.n_tiles;
+    views.push_back(make_view(nl, j, *p));
+    segs.push_back(s);
+    eng->stats.items += s.seg.n_items;
+  }
+  if (tiles > 0x7fffff00ll) return efail(eng, GATSPI_ECAPACITY, "too many tiles in one step");
+  std::memcpy(h + jobs_off, views.data(), views.size() * sizeof(JobView));
+  std::memcpy(h + segs_off, segs.data(), segs.size() * sizeof(MultiSeg));
+  if (bytes) ECK(cudaMemcpyAsync(eng->d_stage, h, bytes, cudaMemcpyHostToDevice, eng->stream));
+  ECK(cudaEventRecord(eng->stage_ev[slot], eng->stream));
+
+  // 4. launches: the propagation step for parts already past level 0, then
+  // level 0 of the admitted parts
+  if (tiles > 0) {
+    ECK(cudaMemsetAsync(eng->d_counter, 0, sizeof(int32_t), eng->stream));
+    MultiParams m{};
+    m.jobs = (const JobView*)(eng->d_stage + jobs_off);
+    m.segs = (const MultiSeg*)(eng->d_stage + segs_off);
+    m.n_segs = (int32_t)segs.size();
+    m.tile_counter = eng->d_counter;
+    switch (eng->tile) {
+      case 128: propagate_multi_kernel<128><<<(unsigned)tiles, 128, 0, eng->stream>>>(m); break;
+      case 512: propagate_multi_kernel<512><<<(unsigned)tiles, 512, 0, eng->stream>>>(m); break;
+      default: propagate_multi_kernel<256><<<(unsigned)tiles, 256, 0, eng->stream>>>(m); break;
+    }
+    ECK(cudaGetLastError());
+    eng->stats.steps++;
+    eng->stats.kernel_launches++;
+  }
+  for (size_t k = 0; k < admitted.size(); ++k) {
+    EPart& p = *admitted[k];
+    EJob& j = *eng->jobs.at(p.job);
+    ENetlist& nl = *eng->nets[j.net];
+    InputParams q{};
+    q.edge_ptr = j.d_edge_ptr; q.edge_time = j.d_edge_time; q.init_in = j.d_init_in;
+    q.in_prefix = (const long long*)(eng->d_stage + pre_off[k]);
+    q.init = p.init; q.off = p.off; q.times = p.times; q.saif_t1 = p.t1; q.saif_tc = p.tc;
+    q.lvl_base = p.lvl_base;
+    long long l0 = 0;
+    const int32_t c0 = p.w0 * j.W, c1 = std::min((p.w0 + p.nw) * j.W, j.C);
+    for (int32_t i = 0; i < nl.r.I; ++i)
+      l0 += j.edge_ptr[(size_t)i * j.C + c1] - j.edge_ptr[(size_t)i * j.C + c0];
+    if (l0 > p.cap) {  // cannot happen: the hint covers level 0
+      return fail_job(eng, j, GATSPI_ECAPACITY, "input edges exceed the part's store");
+    }
+    q.total = l0;
+    q.I = nl.r.I; q.NW = p.nw; q.w0 = p.w0; q.W = j.W; q.C = j.C; q.L = j.L;
+    q.n_items = nl.r.I * p.nw;
+    inputs_kernel<<<(q.n_items + 255) / 256, 256, 0, eng->stream>>>(q);
+    ECK(cudaGetLastError());
+    eng->stats.kernel_launches++;
+  }
+
+  // 5. advance; parts past their last level report status and edge count
+  for (size_t k = 0; k < eng->active.size();) {
+    EPart& p = *eng->active[k];
+    p.level++;
+    if (p.level > p.D) {
+      if (eng->free_slots.empty()) return efail(eng, GATSPI_ESTATE, "no result slot");
+      p.slot = eng->free_slots.back();
+      eng->free_slots.pop_back();
+      if (!eng->free_events.empty()) {
+        p.ev = eng->free_events.back();
+        eng->free_events.pop_back();
+      } else {
+        ECK(cudaEventCreateWithFlags(&p.ev, cudaEventDisableTiming));
+      }
+      PartResult* r = eng->h_results + p.slot;
+      ECK(cudaMemcpyAsync(&r->status, p.status, sizeof(int32_t), cudaMemcpyDeviceToHost, eng->stream));
+      ECK(cudaMemcpyAsync(&r->edges, p.lvl_base + p.D + 1, sizeof(long long), cudaMemcpyDeviceToHost,
+                          eng->stream));
+      ECK(cudaEventRecord(p.ev, eng->stream));
+      eng->finishing.push_back(std::move(eng->active[k]));
+      eng->active.erase(eng->active.begin() + (long)k);
+      continue;
+    }
+    ++k;
+  }
+  for (auto& kv : eng->jobs) {
+    EJob& j = *kv.second;
+    if (j.state == GATSPI_JOB_QUEUED && j.parts_done + (int32_t)0 < j.parts_total) {
+      for (auto& p : eng->active)
+        if (p->job == j.id) { j.state = GATSPI_JOB_RUNNING; break; }
+    }
+  }
+  eng->stats.active = (int32_t)(eng->active.size() + eng->finishing.size());
+  eng->stats.queued = (int32_t)eng->queued.size();
+  if (active_out) *active_out = eng->stats.active;
+  if (queued_out) *queued_out = eng->stats.queued;
+  return GATSPI_OK;
+}
+
+int gatspi_engine_drain(gatspi_engine* eng) {
+  if (!eng) return GATSPI_EINVAL;
+  int rc = GATSPI_OK;
+  for (;;) {
+    int32_t a = 0, q = 0;
+    const int r = gatspi_engine_step(eng, &a, &q);
+    if (r && !rc) rc = r;
+    if (r == GATSPI_ECUDA) return r;
+    if (a == 0 && q == 0) break;
+  }
+  ECK(cudaStreamSynchronize(eng->stream));
+  return rc;
+}
+
+int gatspi_engine_poll(gatspi_engine* eng, int64_t job_id, int32_t* state, int64_t* t0, int64_t* t1,
+                       int64_t* tc) {
+  if (!eng) return GATSPI_EINVAL;
+  auto it = eng->jobs.find(job_id);
+  if (it == eng->jobs.end()) return efail(eng, GATSPI_EINVAL, "unknown job id");
+  EJob& j = *it->second;
+  ECK(cudaSetDevice(eng->device));
+  if (j.state != GATSPI_JOB_FAILED && j.done_recorded) {
+    const cudaError_t q = cudaEventQuery(j.done_ev);
+    if (q == cudaSuccess) j.state = GATSPI_JOB_DONE;
+    else if (q != cudaErrorNotReady) return efail(eng, GATSPI_ECUDA, cudaGetErrorString(q));
+  }
+  if (state) *state = j.state;
+  if (j.state == GATSPI_JOB_DONE && (t0 || t1 || tc)) {
+    const ENetlist& nl = *eng->nets[j.net];
+    const int32_t N = nl.r.N;
+    std::vector<unsigned long long> a(N), b(N);
+    ECK(cudaMemcpy(a.data(), j.d_t1, sizeof(unsigned long long) * N, cudaMemcpyDeviceToHost));
+    ECK(cudaMemcpy(b.data(), j.d_tc, sizeof(unsigned long long) * N, cudaMemcpyDeviceToHost));
+    const int64_t total = (int64_t)j.C * j.L;
+    for (int32_t e = 0; e < N; ++e) {
+      const int32_t n = nl.r.net_int[e];
+      if (t1) t1[e] = (int64_t)a[n];
+      if (t0) t0[e] = total - (int64_t)a[n];
+      if (tc) tc[e] = (int64_t)b[n];
+    }
+  }
+  if (j.state == GATSPI_JOB_FAILED) return efail(eng, GATSPI_OK, j.err);
+  return GATSPI_OK;
+}
+
+int gatspi_engine_release(gatspi_engine* eng, int64_t job_id) {
+  if (!eng) return GATSPI_EINVAL;
+  auto it = eng->jobs.find(job_id);
+  if (it == eng->jobs.end()) return efail(eng, GATSPI_EINVAL, "unknown job id");
+  EJob& j = *it->second;
+  if (j.state != GATSPI_JOB_DONE && j.state != GATSPI_JOB_FAILED)
+    return efail(eng, GATSPI_ESTATE, "job still running");
+  for (auto& p : eng->active)
+    if (p->job == job_id) return efail(eng, GATSPI_ESTATE, "job still has parts in flight");
+  for (auto& p : eng->finishing)
+    if (p->job == job_id) return efail(eng, GATSPI_ESTATE, "job still has parts in flight");
+  ECK(cudaSetDevice(eng->device));
+  free_job_device(j, eng->stream);
+  eng->jobs.erase(it);
+  return GATSPI_OK;
+}
+
+int gatspi_engine_get_stats(gatspi_engine* eng, gatspi_engine_stats* out) {
+  if (!eng || !out) return GATSPI_EINVAL;
+  *out = eng->stats;
+  return GATSPI_OK;
+}
+
+}  // extern "C"

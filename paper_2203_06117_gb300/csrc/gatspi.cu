@@ -1,0 +1,633 @@
+// Host side of the C interface declared in include/gatspi.h: validation,
+// levelization, device memory, the level-by-level launch loop over batches
+// of windows, SAIF and waveform read-back.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "gatspi.h"
+#include "host_common.h"
+#include "kernels.cuh"
+
+using namespace gatspi_dev;
+
+namespace {
+
+constexpr int64_t kAlign = 256;
+
+int64_t align_up(int64_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+}  // namespace
+
+struct gatspi_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  std::string err;
+  size_t arena_limit = 0;
+
+  // netlist in internal order (inputs, then gates sorted by level)
+  int32_t I = 0, G = 0, N = 0, P = 0, D = 0;
+  std::vector<int32_t> gate_ext;   // internal gate -> caller gate
+  std::vector<int32_t> net_int;    // caller net -> internal net
+  std::vector<int32_t> pin_ext;    // internal pin -> caller pin
+  std::vector<int32_t> fanin_ptr, fanin_net, net_level;
+  std::vector<uint16_t> lut;
+  std::vector<int32_t> lvl_gate_begin;  // [D+2]: gates of level l (l >= 1) are
+                                        // lvl_gate_begin[l] .. lvl_gate_begin[l+1]
+  std::vector<int64_t> fanout;          // pins driven by each internal net
+  int32_t max_gate_delay = 0, max_wire_delay = 0;
+  bool have_netlist = false, have_delays = false, have_stim = false, have_result = false;
+
+  int32_t* d_fanin_ptr = nullptr;
+  int32_t* d_fanin_net = nullptr;
+  int32_t* d_net_level = nullptr;
+  uint16_t* d_lut = nullptr;
+  int32_t* d_gate_delay = nullptr;
+  int32_t* d_wire_delay = nullptr;
+  int32_t* d_gate_delta = nullptr;  // delay edit per internal gate, or null
+  int32_t max_edit = 0;
+
+  // stimulus
+  int32_t C = 0, L = 0;
+  std::vector<int64_t> edge_ptr;
+  int64_t* d_edge_ptr = nullptr;
+  int32_t* d_edge_time = nullptr;
+  uint8_t* d_init_in = nullptr;
+  std::vector<uint8_t> init_in;
+
+  // SAIF and status
+  unsigned long long* d_t1 = nullptr;
+  unsigned long long* d_tc = nullptr;
+  int32_t* d_status = nullptr;
+  long long* d_in_prefix = nullptr;
+  int64_t total_time = 0;
+
+  // arena, carved per batch
+  char* d_arena = nullptr;
+  size_t arena_bytes = 0;
+  int64_t times_cap_hint = 0;
+  uint8_t* d_init = nullptr;
+  int32_t* d_off = nullptr;
+  unsigned long long* d_tile_state = nullptr;
+  int32_t* d_tile_counter = nullptr;
+  long long* d_lvl_base = nullptr;
+  int32_t* d_times = nullptr;
+  int64_t times_cap = 0;
+  size_t scratch_bytes = 0;  // tile states + counters (zeroed per batch)
+  std::vector<int64_t> tile_base;  // per level, offset into tile states
+
+  // last simulation
+  int32_t W = 1, batch_w0 = 0, batch_nw = 0, n_windows = 0, tile = 256;
+  gatspi_stats stats{};
+  std::vector<cudaEvent_t> ev;
+};
+
+namespace {
+
+int fail(gatspi_ctx* c, int code, const std::string& msg) {
+  if (c) c->err = msg;
+  return code;
+}
+
+#define CK(call)                                                                      \
+  do {                                                                                \
+    cudaError_t e_ = (call);                                                          \
+    if (e_ != cudaSuccess)                                                            \
+      return fail(ctx, GATSPI_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+template <class T>
+void dfree(T*& p) {
+  if (p) cudaFree(p);
+  p = nullptr;
+}
+
+template <class T>
+int upload(gatspi_ctx* ctx, T*& dst, const T* src, size_t n) {
+  dfree(dst);
+  CK(cudaMalloc(&dst, std::max<size_t>(n, 1) * sizeof(T)));
+  if (src && n) CK(cudaMemcpy(dst, src, n * sizeof(T), cudaMemcpyHostToDevice));
+  return GATSPI_OK;
+}
+
+void free_netlist(gatspi_ctx* c) {
+  dfree(c->d_gate_delta);
+  c->max_edit = 0;
+  dfree(c->d_fanin_ptr); dfree(c->d_fanin_net); dfree(c->d_net_level); dfree(c->d_lut);
+  dfree(c->d_gate_delay); dfree(c->d_wire_delay); dfree(c->d_t1); dfree(c->d_tc);
+  dfree(c->d_in_prefix);
+}
+
+void free_stim(gatspi_ctx* c) {
+  dfree(c->d_edge_ptr); dfree(c->d_edge_time); dfree(c->d_init_in);
+}
+
+void free_arena(gatspi_ctx* c) {
+  dfree(c->d_arena);
+  c->arena_bytes = 0;
+}
+
+// Carve the arena for a batch of NW windows; returns false if it does not fit.
+bool plan_batch(gatspi_ctx* c, int32_t NW, int tile, size_t* need_fixed) {
+  const int64_t N = c->N;
+  int64_t off = 0;
+  const int64_t o_init = off; off = align_up(off + N * NW);
+  const int64_t o_off = off; off = align_up(off + (N * NW + c->D + 2) * 4);
+  const int64_t o_lvl = off; off = align_up(off + (c->D + 2) * 8);
+  const int64_t o_scr = off;
+  c->tile_base.assign(c->D + 2, 0);
+  int64_t tiles = 0;
+  for (int32_t l = 1; l <= c->D; ++l) {
+    c->tile_base[l] = tiles;
+    const int64_t items = (int64_t)(c->lvl_gate_begin[l + 1] - c->lvl_gate_begin[l]) * NW;
+    tiles += (items + tile - 1) / tile;
+  }
+  const int64_t o_cnt = align_up(o_scr + tiles * 8);
+  off = align_up(o_cnt + (c->D + 2) * 4);
+  c->scratch_bytes = (size_t)(off - o_scr);
+  const int64_t o_times = off;
+  *need_fixed = (size_t)o_times;
+  if ((size_t)o_times + 1024 * 4 > c->arena_bytes) return false;
+  char* a = c->d_arena;
+  c->d_init = (uint8_t*)(a + o_init);
+  c->d_off = (int32_t*)(a + o_off);
+  c->d_lvl_base = (long long*)(a + o_lvl);
+  c->d_tile_state = (unsigned long long*)(a + o_scr);
+  c->d_tile_counter = (int32_t*)(a + o_cnt);
+  c->d_times = (int32_t*)(a + o_times);
+  c->times_cap = (int64_t)((c->arena_bytes - (size_t)o_times) / 4);
+  return true;
+}
+
+int ensure_arena(gatspi_ctx* ctx, size_t bytes) {
+  bytes = std::min(bytes, ctx->arena_limit);
+  if (ctx->d_arena && ctx->arena_bytes >= bytes) return GATSPI_OK;
+  free_arena(ctx);
+  cudaError_t e = cudaMalloc(&ctx->d_arena, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    ctx->d_arena = nullptr;
+    return fail(ctx, GATSPI_ENOMEM, std::string("arena allocation of ") + std::to_string(bytes) +
+                                        " bytes failed: " + cudaGetErrorString(e));
+  }
+  ctx->arena_bytes = bytes;
+  return GATSPI_OK;
+}
+
+// Fixed bytes (everything but edge times) for NW windows.
+size_t fixed_bytes(const gatspi_ctx* c, int32_t NW, int tile) {
+  const int64_t N = c->N;
+  int64_t tiles = 0;
+  for (int32_t l = 1; l <= c->D; ++l)
+    tiles += ((int64_t)(c->lvl_gate_begin[l + 1] - c->lvl_gate_begin[l]) * NW + tile - 1) / tile;
+  return (size_t)(align_up(N * NW) + align_up((N * NW + c->D + 2) * 4) + align_up((c->D + 2) * 8) +
+                  align_up(tiles * 8) + align_up((c->D + 2) * 4) + 4096);
+}
+
+}  // namespace
+
+extern "C" {
+
+int gatspi_create(gatspi_ctx** out, int device, size_t arena_bytes) {
+  gatspi_ctx* ctx = nullptr;
+  if (!out) return GATSPI_EINVAL;
+  *out = nullptr;
+  int n = 0;
+  if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) {
+    cudaGetLastError();
+    return GATSPI_EINVAL;
+  }
+  ctx = new gatspi_ctx();
+  ctx->device = device;
+  if (cudaSetDevice(device) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaMalloc(&ctx->d_status, sizeof(int32_t)) != cudaSuccess) {
+    cudaGetLastError();
+    delete ctx;
+    return GATSPI_ECUDA;
+  }
+  size_t free_b = 0, total_b = 0;
+  cudaMemGetInfo(&free_b, &total_b);
+  ctx->arena_limit = arena_bytes ? arena_bytes : (size_t)(0.85 * (double)free_b);
+  *out = ctx;
+  return GATSPI_OK;
+}
+
+int gatspi_destroy(gatspi_ctx* ctx) {
+  if (!ctx) return GATSPI_OK;
+  cudaSetDevice(ctx->device);
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  free_netlist(ctx);
+  free_stim(ctx);
+  free_arena(ctx);
+  dfree(ctx->d_status);
+  for (auto e : ctx->ev) cudaEventDestroy(e);
+  if (ctx->stream) cudaStreamDestroy(ctx->stream);
+  delete ctx;
+  return GATSPI_OK;
+}
+
+const char* gatspi_last_error(gatspi_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+int gatspi_load_netlist(gatspi_ctx* ctx, int32_t num_inputs, int32_t num_gates,
+                        const int32_t* fanin_ptr, const int32_t* fanin_net, const uint16_t* lut) {
+  if (!ctx) return GATSPI_EINVAL;
+  gatspi_host::Prepared r;
+  const std::string why = gatspi_host::prepare_netlist(num_inputs, num_gates, fanin_ptr, fanin_net, lut, &r);
+  if (!why.empty()) return fail(ctx, GATSPI_EINVAL, why);
+  CK(cudaSetDevice(ctx->device));
+  ctx->have_netlist = ctx->have_delays = ctx->have_stim = ctx->have_result = false;
+  free_netlist(ctx);
+  ctx->I = r.I; ctx->G = r.G; ctx->N = r.N; ctx->P = r.P; ctx->D = r.D;
+  ctx->gate_ext = std::move(r.gate_ext);
+  ctx->net_int = std::move(r.net_int);
+  ctx->pin_ext = std::move(r.pin_ext);
+  ctx->fanin_ptr = std::move(r.fanin_ptr);
+  ctx->fanin_net = std::move(r.fanin_net);
+  ctx->net_level = std::move(r.net_level);
+  ctx->lut = std::move(r.lut);
+  ctx->lvl_gate_begin = std::move(r.lvl_gate_begin);
+  ctx->fanout = std::move(r.fanout);
+  int rc;
+  if ((rc = upload(ctx, ctx->d_fanin_ptr, ctx->fanin_ptr.data(), ctx->fanin_ptr.size()))) return rc;
+  if ((rc = upload(ctx, ctx->d_fanin_net, ctx->fanin_net.data(), ctx->fanin_net.size()))) return rc;
+  if ((rc = upload(ctx, ctx->d_net_level, ctx->net_level.data(), ctx->net_level.size()))) return rc;
+  if ((rc = upload(ctx, ctx->d_lut, ctx->lut.data(), ctx->lut.size()))) return rc;
+  if ((rc = upload<unsigned long long>(ctx, ctx->d_t1, nullptr, ctx->N))) return rc;
+  if ((rc = upload<unsigned long long>(ctx, ctx->d_tc, nullptr, ctx->N))) return rc;
+  if ((rc = upload<long long>(ctx, ctx->d_in_prefix, nullptr, ctx->I))) return rc;
+  ctx->have_netlist = true;
+  return GATSPI_OK;
+}
+
+int gatspi_load_delays(gatspi_ctx* ctx, const int32_t* gate_delay, const int32_t* wire_delay) {
+  if (!ctx) return GATSPI_EINVAL;
+  if (!ctx->have_netlist) return fail(ctx, GATSPI_ESTATE, "load a netlist before its delays");
+  gatspi_host::Prepared view;  // only the fields prepare_delays reads
+  view.G = ctx->G; view.P = ctx->P;
+  view.fanin_ptr = ctx->fanin_ptr;
+  view.pin_ext = ctx->pin_ext;
+  std::vector<int32_t> gd, wd;
+  int32_t mg = 0, mw = 0;
+  const std::string why = gatspi_host::prepare_delays(view, gate_delay, wire_delay, &gd, &wd, &mg, &mw);
+  if (!why.empty()) return fail(ctx, GATSPI_EINVAL, why);
+  CK(cudaSetDevice(ctx->device));
+  int rc;
+  if ((rc = upload(ctx, ctx->d_gate_delay, gd.data(), gd.size()))) return rc;
+  if ((rc = upload(ctx, ctx->d_wire_delay, wd.data(), wd.size()))) return rc;
+  ctx->max_gate_delay = mg;
+  ctx->max_wire_delay = mw;
+  dfree(ctx->d_gate_delta);
+  ctx->max_edit = 0;
+  ctx->have_delays = true;
+  ctx->have_result = false;
+  return GATSPI_OK;
+}
+
+int gatspi_set_edit(gatspi_ctx* ctx, int32_t n_edits, const int32_t* edit_gate, const int32_t* edit_delta) {
+  if (!ctx) return GATSPI_EINVAL;
+  if (!ctx->have_delays) return fail(ctx, GATSPI_ESTATE, "load delays before an edit");
+  if (n_edits < 0 || (n_edits > 0 && (!edit_gate || !edit_delta)))
+    return fail(ctx, GATSPI_EINVAL, "bad delay edit arrays");
+  CK(cudaSetDevice(ctx->device));
+  ctx->have_result = false;
+  if (n_edits == 0) {
+    dfree(ctx->d_gate_delta);
+    ctx->max_edit = 0;
+    return GATSPI_OK;
+  }
+  std::vector<int32_t> delta(ctx->G, 0);
+  int32_t mx = 0;
+  for (int32_t k = 0; k < n_edits; ++k) {
+    const int32_t g = edit_gate[k];
+    if (g < 0 || g >= ctx->G) return fail(ctx, GATSPI_EINVAL, "edit names an unknown gate");
+    if (edit_delta[k] < -gatspi_host::kMaxDelay || edit_delta[k] > gatspi_host::kMaxDelay)
+      return fail(ctx, GATSPI_EINVAL, "edit delta outside +-2^24 ps");
+    delta[ctx->net_int[(size_t)ctx->I + g] - ctx->I] = edit_delta[k];
+    mx = std::max(mx, edit_delta[k]);
+  }
+  int rc;
+  if ((rc = upload(ctx, ctx->d_gate_delta, delta.data(), delta.size()))) return rc;
+  ctx->max_edit = mx;
+  return GATSPI_OK;
+}
+
+int gatspi_set_stimulus(gatspi_ctx* ctx, int32_t num_cycles, int32_t cycle_ps, const uint8_t* init,
+                        const int64_t* edge_ptr, const int32_t* edge_time) {
+  if (!ctx) return GATSPI_EINVAL;
+  if (!ctx->have_netlist) return fail(ctx, GATSPI_ESTATE, "load a netlist before the stimulus");
+  const std::string why =
+      gatspi_host::validate_stimulus(ctx->I, num_cycles, cycle_ps, init, edge_ptr, edge_time);
+  if (!why.empty()) return fail(ctx, GATSPI_EINVAL, why);
+  CK(cudaSetDevice(ctx->device));
+  const int64_t n = (int64_t)ctx->I * num_cycles;
+  ctx->have_stim = ctx->have_result = false;
+  free_stim(ctx);
+  ctx->C = num_cycles;
+  ctx->L = cycle_ps;
+  ctx->edge_ptr.assign(edge_ptr, edge_ptr + n + 1);
+  ctx->init_in.assign(init, init + ctx->I);
+  int rc;
+  if ((rc = upload(ctx, ctx->d_edge_ptr, edge_ptr, (size_t)n + 1))) return rc;
+  if ((rc = upload(ctx, ctx->d_edge_time, edge_time, (size_t)edge_ptr[n]))) return rc;
+  if ((rc = upload(ctx, ctx->d_init_in, init, (size_t)ctx->I))) return rc;
+  ctx->have_stim = true;
+  return GATSPI_OK;
+}
+
+int gatspi_simulate(gatspi_ctx* ctx, const gatspi_opts* opts) {
+  if (!ctx) return GATSPI_EINVAL;
+  if (!ctx->have_netlist || !ctx->have_delays || !ctx->have_stim)
+    return fail(ctx, GATSPI_ESTATE, "load a netlist, its delays and a stimulus first");
+  const auto t_start = std::chrono::steady_clock::now();
+  CK(cudaSetDevice(ctx->device));
+  gatspi_opts o{};
+  if (opts) o = *opts;
+  for (int k = 0; k < 4; ++k)
+    if (o.reserved[k]) return fail(ctx, GATSPI_EINVAL, "reserved option fields must be 0");
+  const int32_t W = o.window_cycles ? o.window_cycles : 1;
+  if (W < 1) return fail(ctx, GATSPI_EINVAL, "window_cycles must be >= 1");
+  const int tile = o.tile_items ? o.tile_items : 256;
+  if (tile != 128 && tile != 256 && tile != 512) return fail(ctx, GATSPI_EINVAL, "tile_items must be 128, 256 or 512");
+  if (o.batch_windows < 0) return fail(ctx, GATSPI_EINVAL, "batch_windows must be >= 0");
+  // every time stays below 2^31: window length plus the longest path
+  if (!gatspi_host::horizon_fits(W, ctx->C, ctx->L, ctx->D, ctx->max_gate_delay, ctx->max_wire_delay,
+                                 ctx->max_edit))
+    return fail(ctx, GATSPI_EINVAL, "window length plus path delays could overflow int32 ps");
+  const int32_t n_windows = (ctx->C + W - 1) / W;
+  int32_t NW = o.batch_windows ? std::min(o.batch_windows, n_windows) : n_windows;
+  // per-level item count must fit int32
+  int64_t widest = ctx->I;
+  for (int32_t l = 1; l <= ctx->D; ++l)
+    widest = std::max<int64_t>(widest, ctx->lvl_gate_begin[l + 1] - ctx->lvl_gate_begin[l]);
+  while ((int64_t)widest * NW > 0x7ffffff0ll && NW > 1) NW = (NW + 1) / 2;
+
+  ctx->W = W;
+  ctx->n_windows = n_windows;
+  ctx->tile = tile;
+  ctx->have_result = false;
+  gatspi_stats st{};
+  st.levels = ctx->D;
+  CK(cudaMemsetAsync(ctx->d_t1, 0, sizeof(unsigned long long) * ctx->N, ctx->stream));
+  CK(cudaMemsetAsync(ctx->d_tc, 0, sizeof(unsigned long long) * ctx->N, ctx->stream));
+  const size_t n_ev = (size_t)2 * (ctx->D + 2);
+  if (o.time_kernels && ctx->ev.size() < n_ev) {
+    for (auto e : ctx->ev) cudaEventDestroy(e);
+    ctx->ev.assign(n_ev, nullptr);
+    for (auto& e : ctx->ev) CK(cudaEventCreate(&e));
+  }
+  cudaEvent_t ev_first = o.time_kernels ? ctx->ev[n_ev - 2] : nullptr;
+  cudaEvent_t ev_last = o.time_kernels ? ctx->ev[n_ev - 1] : nullptr;
+  bool first_recorded = false;
+
+  // size the arena: fixed part + room for edges (grown on overflow)
+  auto want_bytes = [&](int32_t nw) {
+    const int64_t items = (int64_t)ctx->N * nw;
+    int64_t edges = std::max<int64_t>(ctx->times_cap_hint, items * 2 + (1 << 20));
+    return fixed_bytes(ctx, nw, tile) + (size_t)edges * 4;
+  };
+  while (NW > 1 && fixed_bytes(ctx, NW, tile) * 2 > ctx->arena_limit) NW = (NW + 1) / 2;
+
+  int32_t w0 = 0;
+  int64_t edges_total = 0;
+  while (w0 < n_windows) {
+    const int32_t nw = std::min(NW, n_windows - w0);
+    int rc = ensure_arena(ctx, want_bytes(nw));
+    if (rc) return rc;
+    size_t fixed = 0;
+    if (!plan_batch(ctx, nw, tile, &fixed)) {
+      if (NW == 1) return fail(ctx, GATSPI_ECAPACITY, "arena too small for one window");
+      NW = (NW + 1) / 2;
+      continue;
+    }
+    // level 0 from the stimulus
+    std::vector<long long> in_prefix(ctx->I);
+    long long l0 = 0;
+    const int32_t c_begin = w0 * W, c_end = std::min((w0 + nw) * W, ctx->C);
+    for (int32_t i = 0; i < ctx->I; ++i) {
+      in_prefix[i] = l0;
+      l0 += ctx->edge_ptr[(size_t)i * ctx->C + c_end] - ctx->edge_ptr[(size_t)i * ctx->C + c_begin];
+    }
+    if (l0 > ctx->times_cap || l0 > 0x7fffffffll) {
+      if (NW > 1) { NW = (NW + 1) / 2; continue; }
+      return fail(ctx, GATSPI_ECAPACITY, "input edges of one window exceed the arena");
+    }
+    CK(cudaMemcpyAsync(ctx->d_in_prefix, in_prefix.data(), sizeof(long long) * ctx->I,
+                       cudaMemcpyHostToDevice, ctx->stream));
+    if (o.time_kernels && !first_recorded) {
+      CK(cudaEventRecord(ev_first, ctx->stream));
+      first_recorded = true;
+    }
+    CK(cudaMemsetAsync(ctx->d_tile_state, 0, ctx->scratch_bytes, ctx->stream));
+    CK(cudaMemsetAsync(ctx->d_status, 0, sizeof(int32_t), ctx->stream));
+    {
+      InputParams q{};
+      q.edge_ptr = ctx->d_edge_ptr; q.edge_time = ctx->d_edge_time; q.init_in = ctx->d_init_in;
+      q.in_prefix = ctx->d_in_prefix; q.init = ctx->d_init; q.off = ctx->d_off; q.times = ctx->d_times;
+      q.saif_t1 = ctx->d_t1; q.saif_tc = ctx->d_tc; q.total = l0; q.lvl_base = ctx->d_lvl_base;
+      q.I = ctx->I; q.NW = nw; q.w0 = w0; q.W = W; q.C = ctx->C; q.L = ctx->L;
+      q.n_items = ctx->I * nw;
+      if (o.time_kernels) CK(cudaEventRecord(ctx->ev[0], ctx->stream));
+      inputs_kernel<<<(q.n_items + 255) / 256, 256, 0, ctx->stream>>>(q);
+      CK(cudaGetLastError());
+      if (o.time_kernels) CK(cudaEventRecord(ctx->ev[1], ctx->stream));
+      st.kernel_launches++;
+    }
+    JobView job{};
+    job.fanin_ptr = ctx->d_fanin_ptr; job.fanin_net = ctx->d_fanin_net; job.lut = ctx->d_lut;
+    job.gate_delay = ctx->d_gate_delay; job.wire_delay = ctx->d_wire_delay;
+    job.net_level = ctx->d_net_level; job.gate_delta = ctx->d_gate_delta;
+    job.init = ctx->d_init; job.off = ctx->d_off; job.times = ctx->d_times; job.lvl_base = ctx->d_lvl_base;
+    job.capacity = ctx->times_cap; job.saif_t1 = ctx->d_t1; job.saif_tc = ctx->d_tc;
+    job.status = ctx->d_status;
+    job.I = ctx->I; job.NW = nw; job.w0 = w0; job.W = W; job.C = ctx->C; job.L = ctx->L;
+    for (int32_t l = 1; l <= ctx->D; ++l) {
+      PropParams p{};
+      p.job = job;
+      p.seg.tile_state = ctx->d_tile_state + ctx->tile_base[l];
+      p.seg.level = l;
+      p.seg.gate_begin = ctx->lvl_gate_begin[l];
+      p.seg.net_end = ctx->I + ctx->lvl_gate_begin[l + 1];
+      p.seg.n_items = (ctx->lvl_gate_begin[l + 1] - ctx->lvl_gate_begin[l]) * nw;
+      p.seg.n_tiles = (p.seg.n_items + tile - 1) / tile;
+      p.tile_counter = ctx->d_tile_counter + l;
+      if (o.time_kernels) CK(cudaEventRecord(ctx->ev[2 * l], ctx->stream));
+      switch (tile) {
+        case 128: propagate_kernel<128><<<p.seg.n_tiles, 128, 0, ctx->stream>>>(p); break;
+        case 512: propagate_kernel<512><<<p.seg.n_tiles, 512, 0, ctx->stream>>>(p); break;
+        default: propagate_kernel<256><<<p.seg.n_tiles, 256, 0, ctx->stream>>>(p); break;
+      }
+      CK(cudaGetLastError());
+      if (o.time_kernels) CK(cudaEventRecord(ctx->ev[2 * l + 1], ctx->stream));
+      st.kernel_launches++;
+      st.prop_launches++;
+      st.items += p.seg.n_items;
+    }
+    if (o.time_kernels) CK(cudaEventRecord(ev_last, ctx->stream));
+    int32_t status = 0;
+    long long lvl_end = 0;
+    CK(cudaMemcpyAsync(&status, ctx->d_status, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(&lvl_end, ctx->d_lvl_base + ctx->D + 1, sizeof(long long), cudaMemcpyDeviceToHost,
+                       ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (status & kStTimeout) return fail(ctx, GATSPI_ETIMEOUT, "a device-side wait ran out");
+    if (status & (kStCapacity | kStOffset | kStCorrupt)) {
+      // undo this batch's SAIF contribution by re-running from scratch
+      const bool can_grow = ctx->arena_bytes < ctx->arena_limit;
+      if (can_grow && !(status & kStOffset)) {
+        ctx->times_cap_hint = std::max<int64_t>(ctx->times_cap_hint, ctx->times_cap) * 2;
+      } else if (NW > 1) {
+        NW = (NW + 1) / 2;
+      } else {
+        return fail(ctx, GATSPI_ECAPACITY, "waveforms of one window exceed the arena");
+      }
+      // restart the whole simulation: SAIF of earlier batches is kept only
+      // if we restart from w0 = 0
+      w0 = 0;
+      edges_total = 0;
+      first_recorded = false;
+      st = gatspi_stats{};
+      st.levels = ctx->D;
+      CK(cudaMemsetAsync(ctx->d_t1, 0, sizeof(unsigned long long) * ctx->N, ctx->stream));
+      CK(cudaMemsetAsync(ctx->d_tc, 0, sizeof(unsigned long long) * ctx->N, ctx->stream));
+      continue;
+    }
+    if (o.time_kernels) {
+      float ms = 0;
+      CK(cudaEventElapsedTime(&ms, ev_first, ev_last));
+      st.device_ms = ms;  // span from the first batch's start to this batch's end
+      CK(cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[1]));
+      st.input_ms += ms;
+      for (int32_t l = 1; l <= ctx->D; ++l) {
+        CK(cudaEventElapsedTime(&ms, ctx->ev[2 * l], ctx->ev[2 * l + 1]));
+        st.prop_ms += ms;
+      }
+    }
+    edges_total += lvl_end;
+    ctx->batch_w0 = w0;
+    ctx->batch_nw = nw;
+    st.batches++;
+    w0 += nw;
+  }
+  st.windows = n_windows;
+  st.batch_windows = NW;
+  st.edges = edges_total;
+  ctx->total_time = (int64_t)ctx->C * ctx->L;
+  // algorithmic bytes: per item and pin 4 + 1 + 4 * edges read, per item
+  // 4 + 1 + 4 * edges written; edges read by a pin = TC of its driving net
+  {
+    std::vector<unsigned long long> tc(ctx->N);
+    CK(cudaMemcpy(tc.data(), ctx->d_tc, sizeof(unsigned long long) * ctx->N, cudaMemcpyDeviceToHost));
+    int64_t b = 5ll * ((int64_t)ctx->P + ctx->G) * n_windows;
+    for (int32_t n = 0; n < ctx->N; ++n)
+      b += 4ll * (int64_t)tc[n] * (ctx->fanout[n] + (n >= ctx->I ? 1 : 0));
+    st.algo_bytes = b;
+  }
+  st.wall_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
+  ctx->stats = st;
+  ctx->have_result = true;
+  return GATSPI_OK;
+}
+
+int gatspi_saif(gatspi_ctx* ctx, int64_t* t0, int64_t* t1, int64_t* tc) {
+  if (!ctx) return GATSPI_EINVAL;
+  if (!ctx->have_result) return fail(ctx, GATSPI_ESTATE, "nothing simulated yet");
+  CK(cudaSetDevice(ctx->device));
+  std::vector<unsigned long long> a(ctx->N), b(ctx->N);
+  CK(cudaMemcpyAsync(a.data(), ctx->d_t1, sizeof(unsigned long long) * ctx->N, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaMemcpyAsync(b.data(), ctx->d_tc, sizeof(unsigned long long) * ctx->N, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  for (int32_t e = 0; e < ctx->N; ++e) {
+    const int32_t n = ctx->net_int[e];
+    if (t1) t1[e] = (int64_t)a[n];
+    if (t0) t0[e] = ctx->total_time - (int64_t)a[n];
+    if (tc) tc[e] = (int64_t)b[n];
+  }
+  return GATSPI_OK;
+}
+
+int gatspi_read_window(gatspi_ctx* ctx, int32_t window, uint8_t* init, int64_t* ptr, int32_t* times,
+                       int64_t cap, int64_t* total) {
+  if (!ctx) return GATSPI_EINVAL;
+  if (!ctx->have_result) return fail(ctx, GATSPI_ESTATE, "nothing simulated yet");
+  if (!init || !ptr) return fail(ctx, GATSPI_EINVAL, "null output array");
+  if (window < ctx->batch_w0 || window >= ctx->batch_w0 + ctx->batch_nw)
+    return fail(ctx, GATSPI_ESTATE, "window " + std::to_string(window) + " is not in the resident batch [" +
+                                        std::to_string(ctx->batch_w0) + ", " +
+                                        std::to_string(ctx->batch_w0 + ctx->batch_nw) + ")");
+  CK(cudaSetDevice(ctx->device));
+  const int32_t N = ctx->N, w = window - ctx->batch_w0;
+  int32_t* d_cnt = nullptr;
+  uint8_t* d_iv = nullptr;
+  long long* d_dst = nullptr;
+  int32_t* d_out = nullptr;
+  int rc = GATSPI_OK;
+  std::vector<int32_t> cnt(N);
+  std::vector<uint8_t> iv(N);
+  std::vector<long long> dst(N);
+  int64_t tot = 0;
+  auto cleanup = [&]() { dfree(d_cnt); dfree(d_iv); dfree(d_dst); dfree(d_out); };
+  do {
+    if (cudaMalloc(&d_cnt, sizeof(int32_t) * N) != cudaSuccess || cudaMalloc(&d_iv, N) != cudaSuccess ||
+        cudaMalloc(&d_dst, sizeof(long long) * N) != cudaSuccess) {
+      cudaGetLastError();
+      rc = fail(ctx, GATSPI_ENOMEM, "read-back buffers");
+      break;
+    }
+    window_counts_kernel<<<(N + 255) / 256, 256, 0, ctx->stream>>>(N, ctx->batch_nw, w, ctx->d_net_level,
+                                                                   ctx->d_off, ctx->d_init, d_cnt, d_iv);
+    if (cudaMemcpyAsync(cnt.data(), d_cnt, sizeof(int32_t) * N, cudaMemcpyDeviceToHost, ctx->stream) ||
+        cudaMemcpyAsync(iv.data(), d_iv, N, cudaMemcpyDeviceToHost, ctx->stream) ||
+        cudaStreamSynchronize(ctx->stream)) {
+      rc = fail(ctx, GATSPI_ECUDA, "read-back copy failed");
+      break;
+    }
+    // caller order
+    ptr[0] = 0;
+    for (int32_t e = 0; e < N; ++e) {
+      const int32_t n = ctx->net_int[e];
+      init[e] = iv[n];
+      ptr[e + 1] = ptr[e] + cnt[n];
+    }
+    tot = ptr[N];
+    if (total) *total = tot;
+    if (!times) break;
+    if (cap < tot) {
+      rc = fail(ctx, GATSPI_ECAPACITY, "times buffer too small: need " + std::to_string(tot));
+      break;
+    }
+    for (int32_t e = 0; e < N; ++e) dst[ctx->net_int[e]] = ptr[e];
+    if (cudaMalloc(&d_out, sizeof(int32_t) * std::max<int64_t>(tot, 1)) != cudaSuccess) {
+      cudaGetLastError();
+      rc = fail(ctx, GATSPI_ENOMEM, "read-back buffers");
+      break;
+    }
+    if (cudaMemcpyAsync(d_dst, dst.data(), sizeof(long long) * N, cudaMemcpyHostToDevice, ctx->stream)) {
+      rc = fail(ctx, GATSPI_ECUDA, "read-back copy failed");
+      break;
+    }
+    window_gather_kernel<<<(N + 255) / 256, 256, 0, ctx->stream>>>(N, ctx->batch_nw, w, ctx->d_net_level,
+                                                                   ctx->d_off, ctx->d_lvl_base, ctx->d_times,
+                                                                   d_dst, d_out);
+    if (cudaMemcpyAsync(times, d_out, sizeof(int32_t) * tot, cudaMemcpyDeviceToHost, ctx->stream) ||
+        cudaStreamSynchronize(ctx->stream)) {
+      rc = fail(ctx, GATSPI_ECUDA, "read-back copy failed");
+      break;
+    }
+  } while (0);
+  cleanup();
+  return rc;
+}
+
+int gatspi_get_stats(gatspi_ctx* ctx, gatspi_stats* out) {
+  if (!ctx || !out) return GATSPI_EINVAL;
+  *out = ctx->stats;
+  return GATSPI_OK;
+}
+
+}  // extern "C"
