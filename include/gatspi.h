@@ -66,12 +66,15 @@ typedef struct gatspi_opts {
   int32_t window_cycles; /* W: cycles per independent window (default 1) */
   int32_t batch_windows; /* windows resident on the device at once; 0 = all
                             that fit in the arena (halved on overflow) */
-  int32_t tile_items;    /* (gate, window) items per thread block: 128, 256
-                            or 512; 0 = 256 */
+  int32_t tile_items;    /* threads per block of the propagation kernel:
+                            128, 256 or 512; 0 = 256 */
   int32_t time_kernels;  /* 1 = time every propagation launch with CUDA
                             events on the library's stream (read back with
                             gatspi_get_stats) */
-  int32_t reserved[4];   /* must be 0 */
+  int32_t items_per_thread; /* consecutive windows of one gate per thread:
+                               1, 2, 4 or 8 (at most 4 with 512 threads);
+                               0 = 4 */
+  int32_t reserved[3];   /* must be 0 */
 } gatspi_opts;
 
 /* Figures of the last gatspi_simulate call. */
@@ -211,11 +214,13 @@ int gatspi_get_stats(gatspi_ctx* ctx, gatspi_stats* out);
 typedef struct gatspi_engine gatspi_engine;
 
 typedef struct gatspi_engine_opts {
-  int32_t tile_items;  /* items per block for every launch: 128, 256, 512;
+  int32_t tile_items;  /* threads per block for every launch: 128, 256, 512;
                           0 = 256 */
   int32_t max_active;  /* parts in flight at once; 0 = 1024 */
   int64_t part_items;  /* max (gate, window) items of one part; 0 = 2^28 */
-  int32_t reserved[4]; /* must be 0 */
+  int32_t items_per_thread; /* 1, 2, 4, 8 (at most 4 with 512 threads);
+                               0 = 4 */
+  int32_t reserved[3]; /* must be 0 */
 } gatspi_engine_opts;
 
 typedef struct gatspi_engine_stats {

@@ -81,12 +81,13 @@ def build(force: bool = False, nvcc: str = "nvcc") -> str:
 class gatspi_opts(ctypes.Structure):
     _fields_ = [("window_cycles", ctypes.c_int32), ("batch_windows", ctypes.c_int32),
                 ("tile_items", ctypes.c_int32), ("time_kernels", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 4)]
+                ("items_per_thread", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
 
 
 class gatspi_engine_opts(ctypes.Structure):
     _fields_ = [("tile_items", ctypes.c_int32), ("max_active", ctypes.c_int32),
-                ("part_items", ctypes.c_int64), ("reserved", ctypes.c_int32 * 4)]
+                ("part_items", ctypes.c_int64), ("items_per_thread", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 3)]
 
 
 class gatspi_engine_stats(ctypes.Structure):
@@ -211,8 +212,10 @@ def gatspi_set_stimulus(ctx, num_cycles, cycle_ps, init, edge_ptr, edge_time) ->
                                           _ptr(et)))
 
 
-def gatspi_simulate(ctx, window_cycles=0, batch_windows=0, tile_items=0, time_kernels=0) -> None:
-    o = gatspi_opts(int(window_cycles), int(batch_windows), int(tile_items), int(time_kernels))
+def gatspi_simulate(ctx, window_cycles=0, batch_windows=0, tile_items=0, time_kernels=0,
+                    items_per_thread=0) -> None:
+    o = gatspi_opts(int(window_cycles), int(batch_windows), int(tile_items), int(time_kernels),
+                    int(items_per_thread))
     _check(ctx, lib().gatspi_simulate(ctx, ctypes.byref(o)))
 
 
@@ -293,9 +296,10 @@ def _echeck(eng, rc):
         raise GatspiError(rc, lib().gatspi_engine_last_error(eng).decode() if eng else "")
 
 
-def gatspi_engine_create(device=0, arena_bytes=0, tile_items=0, max_active=0, part_items=0):
+def gatspi_engine_create(device=0, arena_bytes=0, tile_items=0, max_active=0, part_items=0,
+                         items_per_thread=0):
     h = ctypes.c_void_p()
-    o = gatspi_engine_opts(int(tile_items), int(max_active), int(part_items))
+    o = gatspi_engine_opts(int(tile_items), int(max_active), int(part_items), int(items_per_thread))
     rc = lib().gatspi_engine_create(ctypes.byref(h), int(device), int(arena_bytes), ctypes.byref(o))
     if rc != OK:
         raise GatspiError(rc, f"cannot create an engine on device {device}")

@@ -88,7 +88,8 @@ struct gatspi_engine {
   std::string err;
   size_t budget = 0, in_use = 0;
   gatspi_engine_opts opts{};
-  int tile = 256;
+  int nt = 256, ipt = 4;
+  int tile = 1024;  // items per block
   std::vector<std::unique_ptr<ENetlist>> nets;
   std::map<int64_t, std::unique_ptr<EJob>> jobs;
   int64_t next_job = 1;
@@ -321,15 +322,20 @@ int gatspi_engine_create(gatspi_engine** out, int device, size_t arena_bytes, co
   }
   gatspi_engine_opts o{};
   if (opts) o = *opts;
-  for (int k = 0; k < 4; ++k)
+  for (int k = 0; k < 3; ++k)
     if (o.reserved[k]) return GATSPI_EINVAL;
-  const int tile = o.tile_items ? o.tile_items : 256;
-  if (tile != 128 && tile != 256 && tile != 512) return GATSPI_EINVAL;
+  const int nt = o.tile_items ? o.tile_items : 256;
+  const int ipt = o.items_per_thread ? o.items_per_thread : 4;
+  if ((nt != 128 && nt != 256 && nt != 512) || (ipt != 1 && ipt != 2 && ipt != 4 && ipt != 8) ||
+      (nt == 512 && ipt == 8))
+    return GATSPI_EINVAL;
   if (o.max_active < 0 || o.part_items < 0) return GATSPI_EINVAL;
   auto* eng = new gatspi_engine();
   eng->device = device;
   eng->opts = o;
-  eng->tile = tile;
+  eng->nt = nt;
+  eng->ipt = ipt;
+  eng->tile = nt * ipt;
   if (!eng->opts.max_active) eng->opts.max_active = 1024;
   if (!eng->opts.part_items) eng->opts.part_items = 1ll << 28;
   if (cudaSetDevice(device) != cudaSuccess ||
@@ -615,11 +621,8 @@ int gatspi_engine_step(gatspi_engine* eng, int32_t* active_out, int32_t* queued_
     m.segs = (const MultiSeg*)(eng->d_stage + segs_off);
     m.n_segs = (int32_t)segs.size();
     m.tile_counter = eng->d_counter;
-    switch (eng->tile) {
-      case 128: propagate_multi_kernel<128><<<(unsigned)tiles, 128, 0, eng->stream>>>(m); break;
-      case 512: propagate_multi_kernel<512><<<(unsigned)tiles, 512, 0, eng->stream>>>(m); break;
-      default: propagate_multi_kernel<256><<<(unsigned)tiles, 256, 0, eng->stream>>>(m); break;
-    }
+    MultiLaunch go{&m, (unsigned)tiles, eng->stream};
+    launch_variant(eng->nt, eng->ipt, go);
     ECK(cudaGetLastError());
     eng->stats.steps++;
     eng->stats.kernel_launches++;

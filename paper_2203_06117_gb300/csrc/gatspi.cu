@@ -348,12 +348,17 @@ int gatspi_simulate(gatspi_ctx* ctx, const gatspi_opts* opts) {
   CK(cudaSetDevice(ctx->device));
   gatspi_opts o{};
   if (opts) o = *opts;
-  for (int k = 0; k < 4; ++k)
+  for (int k = 0; k < 3; ++k)
     if (o.reserved[k]) return fail(ctx, GATSPI_EINVAL, "reserved option fields must be 0");
   const int32_t W = o.window_cycles ? o.window_cycles : 1;
   if (W < 1) return fail(ctx, GATSPI_EINVAL, "window_cycles must be >= 1");
-  const int tile = o.tile_items ? o.tile_items : 256;
-  if (tile != 128 && tile != 256 && tile != 512) return fail(ctx, GATSPI_EINVAL, "tile_items must be 128, 256 or 512");
+  const int nt = o.tile_items ? o.tile_items : 256;
+  const int ipt = o.items_per_thread ? o.items_per_thread : 4;
+  if ((nt != 128 && nt != 256 && nt != 512) || (ipt != 1 && ipt != 2 && ipt != 4 && ipt != 8) ||
+      (nt == 512 && ipt == 8))
+    return fail(ctx, GATSPI_EINVAL, "tile_items must be 128, 256 or 512 and items_per_thread 1, 2, 4 or 8 "
+                                    "(at most 4 with 512)");
+  const int tile = nt * ipt;  // items per block
   if (o.batch_windows < 0) return fail(ctx, GATSPI_EINVAL, "batch_windows must be >= 0");
   // every time stays below 2^31: window length plus the longest path
   if (!gatspi_host::horizon_fits(W, ctx->C, ctx->L, ctx->D, ctx->max_gate_delay, ctx->max_wire_delay,
@@ -457,11 +462,8 @@ int gatspi_simulate(gatspi_ctx* ctx, const gatspi_opts* opts) {
       p.seg.n_tiles = (p.seg.n_items + tile - 1) / tile;
       p.tile_counter = ctx->d_tile_counter + l;
       if (o.time_kernels) CK(cudaEventRecord(ctx->ev[2 * l], ctx->stream));
-      switch (tile) {
-        case 128: propagate_kernel<128><<<p.seg.n_tiles, 128, 0, ctx->stream>>>(p); break;
-        case 512: propagate_kernel<512><<<p.seg.n_tiles, 512, 0, ctx->stream>>>(p); break;
-        default: propagate_kernel<256><<<p.seg.n_tiles, 256, 0, ctx->stream>>>(p); break;
-      }
+      SingleLaunch go{&p, ctx->stream};
+      launch_variant(nt, ipt, go);
       CK(cudaGetLastError());
       if (o.time_kernels) CK(cudaEventRecord(ctx->ev[2 * l + 1], ctx->stream));
       st.kernel_launches++;

@@ -31,7 +31,10 @@ namespace gatspi_dev {
 namespace {  // every translation unit gets its own copy of the kernels
 
 constexpr int32_t kInf = 0x7fffffff;
-constexpr int kCap = 8;  // output edges per thread staged in shared memory
+// output edges per thread staged in shared memory (two NT x cap int32
+// buffers per block stay under the 48 KB static limit)
+template <int NT>
+__host__ __device__ constexpr int staging_cap() { return NT >= 512 ? 8 : 16; }
 
 // status bits (device -> host)
 constexpr int kStCapacity = 1;  // arena too small for this batch
@@ -43,7 +46,7 @@ constexpr int kStOffset = 8;    // a level's edges exceed the int32 offset range
 constexpr unsigned long long kFlagAggregate = 1ull << 62;
 constexpr unsigned long long kFlagPrefix = 2ull << 62;
 constexpr unsigned long long kValueMask = (1ull << 62) - 1;
-constexpr long long kSpinLimit = 1ll << 22;  // bounded wait (~1 s with backoff)
+constexpr long long kSpinLimit = 1ll << 20;  // bounded wait (well under a second)
 
 // One simulation job as the kernels see it: a netlist with its delays, one
 // batch of windows of its stimulus, and where its waveforms and SAIF go.
@@ -202,11 +205,15 @@ __device__ __forceinline__ void run_gate(Pin (&pin)[K], uint32_t lut,
   t1 = acc;
 }
 
-template <int TILE>
+// Appends a thread's output edges to its column of the block's staging
+// buffer (element k of the column at [k * NT]); edges past the cap are dropped
+// and the thread re-simulates straight to global memory later.
+template <int NT>
 struct SmemSink {
-  int32_t* col;  // this thread's column of the staging buffer
+  int32_t* col;
+  int32_t pos;  // edges already staged by this thread's earlier items
   __device__ __forceinline__ void put(int k, int32_t t) {
-    if (k < kCap) col[k * TILE] = t;
+    if (pos + k < staging_cap<NT>()) col[(pos + k) * NT] = t;
   }
 };
 
@@ -275,44 +282,74 @@ __device__ __forceinline__ void simulate_item(const JobView& J, int32_t g, int32
   }
 }
 
-// One tile (TILE consecutive items of a level, gate-major) of one job:
-// simulate, scan the edge counts, find the tile's offset by look-back, write
-// records and edges, and add the tile's SAIF.  Called by every thread of the
-// block; `tile` is the tile's index inside its level.
-template <int TILE>
+// One tile of one job's level: NT threads x IPT items, items in
+// gate-major, window-minor order, thread t taking IPT consecutive items
+// (consecutive windows of one gate, so its gate metadata is fetched once
+// and its records and edges are contiguous).  Simulate, scan the edge
+// counts, find the tile's offset by look-back, write records and edges, and
+// add the tile's SAIF.  Called by every thread of the block.
+template <int NT, int IPT>
 __device__ __forceinline__ void propagate_tile(const JobView& J, const SegView& S, int32_t tile) {
-  constexpr int NWARP = TILE / 32;
-  __shared__ int32_t s_scr[kCap * TILE];
-  __shared__ int32_t s_cmp[kCap * TILE];
-  __shared__ unsigned long long s_t1[TILE];
-  __shared__ unsigned int s_tc[TILE];
+  constexpr int NWARP = NT / 32;
+  constexpr int TILE = NT * IPT;
+  constexpr int kCap = staging_cap<NT>();
+  __shared__ int32_t s_scr[kCap * NT];
+  __shared__ int32_t s_cmp[kCap * NT];
   __shared__ long long s_wsum[NWARP];
   __shared__ int32_t s_over;
   __shared__ long long s_prefix, s_base;
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  s_t1[tid] = 0;
-  s_tc[tid] = 0;
   if (tid == 0) {
     s_over = 0;
     s_base = J.lvl_base[S.level];
   }
   __syncthreads();
-  const int32_t r = tile * TILE + tid;
-  const bool valid = r < S.n_items;
-  const int32_t gl_first = (tile * TILE) / J.NW;
-  int32_t count = 0, t1 = 0, gl = 0, w = 0;
-  uint32_t y0 = 0;
-  if (valid) {
-    gl = r / J.NW;
-    w = r - gl * J.NW;
-    SmemSink<TILE> sink{s_scr + tid};
-    simulate_item(J, S.gate_begin + gl, w, sink, count, t1, y0);
-    if (count > kCap) s_over = 1;
+  const int32_t r0 = tile * TILE + tid * IPT;  // this thread's first item
+  const int32_t n_mine = max(0, min(IPT, S.n_items - r0));
+  int32_t cnt[IPT];
+  uint32_t y0s = 0;
+  int32_t total = 0;
+  // SAIF partial sums for the thread's current gate
+  int32_t cur_gl = -1;
+  long long acc_t1 = 0, acc_tc = 0;
+  int32_t gl = 0, w = 0;
+  if (n_mine > 0) {
+    gl = r0 / J.NW;
+    w = r0 - gl * J.NW;
   }
+#pragma unroll
+  for (int m = 0; m < IPT; ++m) {
+    cnt[m] = 0;
+    if (m < n_mine) {
+      if (gl != cur_gl) {
+        if (cur_gl >= 0) {  // gate changed inside the thread's items (small NW)
+          const long long n = (long long)J.I + S.gate_begin + cur_gl;
+          if (acc_t1) atomicAdd(J.saif_t1 + n, (unsigned long long)acc_t1);
+          if (acc_tc) atomicAdd(J.saif_tc + n, (unsigned long long)acc_tc);
+        }
+        cur_gl = gl;
+        acc_t1 = acc_tc = 0;
+      }
+      SmemSink<NT> sink{s_scr + tid, total};
+      int32_t c = 0, t1 = 0;
+      uint32_t y0 = 0;
+      simulate_item(J, S.gate_begin + gl, w, sink, c, t1, y0);
+      cnt[m] = c;
+      total += c;
+      y0s |= y0 << m;
+      acc_t1 += t1;
+      acc_tc += c;
+      if (++w == J.NW) {
+        w = 0;
+        ++gl;
+      }
+    }
+  }
+  if (total > kCap) s_over = 1;
 
-  // block-wide exclusive scan of the edge counts
-  int32_t incl = count;
+  // block-wide exclusive scan of the per-thread edge counts
+  int32_t incl = total;
 #pragma unroll
   for (int d = 1; d < 32; d <<= 1) {
     const int32_t v = __shfl_up_sync(0xffffffffu, incl, d);
@@ -330,7 +367,7 @@ __device__ __forceinline__ void propagate_tile(const JobView& J, const SegView& 
     if (lane < NWARP) s_wsum[lane] = v;
   }
   __syncthreads();
-  const long long excl_local = (warp ? s_wsum[warp - 1] : 0) + incl - count;
+  const long long excl_local = (warp ? s_wsum[warp - 1] : 0) + incl - total;
   const long long aggregate = s_wsum[NWARP - 1];
 
   // decoupled look-back: this block's offset among all blocks of the level
@@ -375,83 +412,96 @@ __device__ __forceinline__ void propagate_tile(const JobView& J, const SegView& 
   const long long base = s_base;
   const long long my_off = prefix + excl_local;
 
-  if (valid) {
-    const long long n = (long long)J.I + S.gate_begin + gl;
-    if (my_off + count > 0x7fffffffll) atomicOr(J.status, kStOffset);
-    J.off[n * J.NW + w + S.level] = (int32_t)my_off;
-    J.init[n * J.NW + w] = (uint8_t)y0;
+  // records: offset and start value of every item; a level's record index
+  // is linear in the item index
+  {
+    const long long rec = ((long long)J.I + S.gate_begin) * J.NW + r0;
+    long long o = my_off;
+#pragma unroll
+    for (int m = 0; m < IPT; ++m) {
+      if (m < n_mine) {
+        J.off[rec + S.level + m] = (int32_t)o;
+        J.init[rec + m] = (uint8_t)((y0s >> m) & 1u);
+        o += cnt[m];
+      }
+    }
+    if (n_mine > 0 && o > 0x7fffffffll) atomicOr(J.status, kStOffset);
   }
   if (tile == S.n_tiles - 1 && tid == 0) {
-    const long long total = prefix + aggregate;
-    if (total > 0x7fffffffll) atomicOr(J.status, kStOffset);
-    J.off[(long long)S.net_end * J.NW + S.level] = (int32_t)total;
-    J.lvl_base[S.level + 1] = base + total;
-    if (base + total > J.capacity) atomicOr(J.status, kStCapacity);
+    const long long tot = prefix + aggregate;
+    if (tot > 0x7fffffffll) atomicOr(J.status, kStOffset);
+    J.off[(long long)S.net_end * J.NW + S.level] = (int32_t)tot;
+    J.lvl_base[S.level + 1] = base + tot;
+    if (base + tot > J.capacity) atomicOr(J.status, kStCapacity);
   }
 
-  // store the edges
+  // edges
   int32_t* dst = J.times + base + prefix;
   const long long room = J.capacity - base - prefix;  // elements left in the arena
   if (!s_over) {
-    for (int k = 0; k < count; ++k) s_cmp[excl_local + k] = s_scr[k * TILE + tid];
+    for (int k = 0; k < total; ++k) s_cmp[excl_local + k] = s_scr[k * NT + tid];
     __syncthreads();
     const long long n = aggregate < room ? aggregate : (room > 0 ? room : 0);
-    for (long long j = tid; j < n; j += TILE) dst[j] = s_cmp[j];
-  } else if (valid) {
-    if (count <= kCap) {
-      for (int k = 0; k < count; ++k)
-        if (excl_local + k < room) dst[excl_local + k] = s_scr[k * TILE + tid];
+    for (long long j = tid; j < n; j += NT) dst[j] = s_cmp[j];
+  } else if (n_mine > 0) {
+    if (total <= kCap) {
+      for (int k = 0; k < total; ++k)
+        if (excl_local + k < room) dst[excl_local + k] = s_scr[k * NT + tid];
     } else {
-      GlobalSink gs{dst + excl_local, room - excl_local};
-      int32_t c2, t2;
-      uint32_t y2;
-      simulate_item(J, S.gate_begin + gl, w, gs, c2, t2, y2);
+      // more edges than the staging column holds: simulate again, straight
+      // to the final positions
+      int32_t g2 = r0 / J.NW, w2 = r0 - g2 * J.NW;
+      long long o = excl_local;
+      for (int m = 0; m < n_mine; ++m) {
+        GlobalSink gs{dst + o, room - o};
+        int32_t c2, t2;
+        uint32_t y2;
+        simulate_item(J, S.gate_begin + g2, w2, gs, c2, t2, y2);
+        o += c2;
+        if (++w2 == J.NW) {
+          w2 = 0;
+          ++g2;
+        }
+      }
     }
   }
 
-  // SAIF: sum T1 and TC per gate inside the block, one atomic per gate
-  const int slot = gl - gl_first;
-  const int32_t g_lane0 = __shfl_sync(0xffffffffu, gl, 0);
-  const bool uniform = __all_sync(0xffffffffu, !valid || gl == g_lane0);
+  // SAIF: the thread's last gate; one atomic per warp when the warp agrees
+  // (every lane takes part in every shuffle)
+  const int32_t g_lane0 = __shfl_sync(0xffffffffu, cur_gl, 0);
+  const bool uniform = __all_sync(0xffffffffu, cur_gl < 0 || cur_gl == g_lane0);
   if (uniform) {
-    long long a = t1, c = count;
+    long long a = acc_t1, c = acc_tc;
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1) {
       a += __shfl_xor_sync(0xffffffffu, a, d);
       c += __shfl_xor_sync(0xffffffffu, c, d);
     }
-    if (lane == 0 && __shfl_sync(0xffffffffu, valid ? 1 : 0, 0) && (a | c)) {
-      atomicAdd(s_t1 + (g_lane0 - gl_first), (unsigned long long)a);
-      atomicAdd(s_tc + (g_lane0 - gl_first), (unsigned int)c);
+    if (lane == 0 && g_lane0 >= 0) {
+      const long long n = (long long)J.I + S.gate_begin + g_lane0;
+      if (a) atomicAdd(J.saif_t1 + n, (unsigned long long)a);
+      if (c) atomicAdd(J.saif_tc + n, (unsigned long long)c);
     }
-  } else if (valid) {
-    atomicAdd(s_t1 + slot, (unsigned long long)t1);
-    atomicAdd(s_tc + slot, (unsigned int)count);
-  }
-  __syncthreads();
-  const int32_t last_r = min(tile * TILE + TILE, S.n_items) - 1;
-  const int32_t n_gates_tile = last_r / J.NW - gl_first + 1;
-  for (int j = tid; j < n_gates_tile; j += TILE) {
-    const long long n = (long long)J.I + S.gate_begin + gl_first + j;
-    if (s_t1[j]) atomicAdd(J.saif_t1 + n, s_t1[j]);
-    if (s_tc[j]) atomicAdd(J.saif_tc + n, (unsigned long long)s_tc[j]);
+  } else if (cur_gl >= 0) {
+    const long long n = (long long)J.I + S.gate_begin + cur_gl;
+    if (acc_t1) atomicAdd(J.saif_t1 + n, (unsigned long long)acc_t1);
+    if (acc_tc) atomicAdd(J.saif_tc + n, (unsigned long long)acc_tc);
   }
 }
 
-
-template <int TILE>
-__global__ void __launch_bounds__(TILE) propagate_kernel(const __grid_constant__ PropParams p) {
+template <int NT, int IPT>
+__global__ void __launch_bounds__(NT) propagate_kernel(const __grid_constant__ PropParams p) {
   __shared__ int32_t s_tile;
   if (threadIdx.x == 0) s_tile = atomicAdd(p.tile_counter, 1);
   __syncthreads();
-  propagate_tile<TILE>(p.job, p.seg, s_tile);
+  propagate_tile<NT, IPT>(p.job, p.seg, s_tile);
 }
 
 // Several jobs (each at its own level) in one launch: tiles are taken in
 // launch order and mapped to (job, level) segments, each segment with its
 // own look-back chain.
-template <int TILE>
-__global__ void __launch_bounds__(TILE) propagate_multi_kernel(const __grid_constant__ MultiParams m) {
+template <int NT, int IPT>
+__global__ void __launch_bounds__(NT) propagate_multi_kernel(const __grid_constant__ MultiParams m) {
   __shared__ JobView s_job;
   __shared__ SegView s_seg;
   __shared__ int32_t s_tile;
@@ -467,7 +517,43 @@ __global__ void __launch_bounds__(TILE) propagate_multi_kernel(const __grid_cons
     s_tile = t - m.segs[lo].tile_begin;
   }
   __syncthreads();
-  propagate_tile<TILE>(s_job, s_seg, s_tile);
+  propagate_tile<NT, IPT>(s_job, s_seg, s_tile);
+}
+
+// Host-side launchers of the two propagation kernels for one compiled
+// (threads, items per thread) variant.
+struct SingleLaunch {
+  const PropParams* p;
+  cudaStream_t s;
+  template <int NT, int IPT>
+  void go() { propagate_kernel<NT, IPT><<<p->seg.n_tiles, NT, 0, s>>>(*p); }
+};
+
+struct MultiLaunch {
+  const MultiParams* m;
+  unsigned grid;
+  cudaStream_t s;
+  template <int NT, int IPT>
+  void go() { propagate_multi_kernel<NT, IPT><<<grid, NT, 0, s>>>(*m); }
+};
+
+// Launch one of the compiled (threads, items per thread) variants.
+template <class Launch>
+inline bool launch_variant(int nt, int ipt, Launch&& launch) {
+  switch (nt * 16 + ipt) {
+    case 128 * 16 + 1: launch.template go<128, 1>(); return true;
+    case 128 * 16 + 2: launch.template go<128, 2>(); return true;
+    case 128 * 16 + 4: launch.template go<128, 4>(); return true;
+    case 128 * 16 + 8: launch.template go<128, 8>(); return true;
+    case 256 * 16 + 1: launch.template go<256, 1>(); return true;
+    case 256 * 16 + 2: launch.template go<256, 2>(); return true;
+    case 256 * 16 + 4: launch.template go<256, 4>(); return true;
+    case 256 * 16 + 8: launch.template go<256, 8>(); return true;
+    case 512 * 16 + 1: launch.template go<512, 1>(); return true;
+    case 512 * 16 + 2: launch.template go<512, 2>(); return true;
+    case 512 * 16 + 4: launch.template go<512, 4>(); return true;
+    default: return false;
+  }
 }
 
 // Level 0: the inputs' records for the batch, read straight from the
@@ -531,6 +617,7 @@ __global__ void inputs_kernel(const InputParams q) {
     q.lvl_base[1] = q.total;
   }
   const int32_t i0 = __shfl_sync(0xffffffffu, i, 0);
+  const int lane0_valid = __shfl_sync(0xffffffffu, valid ? 1 : 0, 0);
   const bool uniform = __all_sync(0xffffffffu, !valid || i == i0);
   if (uniform) {
     long long c = cnt;
@@ -539,7 +626,7 @@ __global__ void inputs_kernel(const InputParams q) {
       t1 += __shfl_xor_sync(0xffffffffu, t1, d);
       c += __shfl_xor_sync(0xffffffffu, c, d);
     }
-    if (lane == 0 && __shfl_sync(0xffffffffu, valid ? 1 : 0, 0)) {
+    if (lane == 0 && lane0_valid) {
       if (t1) atomicAdd(q.saif_t1 + i0, (unsigned long long)t1);
       if (c) atomicAdd(q.saif_tc + i0, (unsigned long long)c);
     }

@@ -200,7 +200,7 @@ def test_small_arena_retries_then_matches():
         sim.simulate()
         assert sim.stats()["batches"] > 1
         assert_saif_equal(sim, ref)
-    with gs.Simulator(wl.netlist, wl.delays, wl.stim, arena_bytes=64 << 10) as sim:
+    with gs.Simulator(wl.netlist, wl.delays, wl.stim, arena_bytes=12 << 10) as sim:
         with pytest.raises(gs.GatspiError) as e:
             sim.simulate()
         assert e.value.code == gs.ECAPACITY
