@@ -235,7 +235,7 @@ def _config(args):
     return {"workload": "mid: 200k gates, depth 60, 512 inputs, 10,000 cycles of 1,000 ps, "
                         "fanin 1-4, geometric fanout mean 2.5, toggle p=0.3, 5% pulses (20% narrow), "
                         "COND on XOR2/MUX2, delays 2-120 ps, seed 1",
-            "gates": 200_000, "cycles": 10_000, "window_cycles": 1, "tile_items": args.tile,
+            "gates": 200_000, "cycles": 10_000, "window_cycles": 1,
             "parallelism": f"replicas x{args.gpus}", "l2": "inputs larger than L2 (waveform store ~20 GB)"}
 
 
@@ -253,7 +253,7 @@ def run_batched_mode(args):
     nets, specs = gen.batched_workload(seed=SEED, scale=args.scale)
     work = sum(nets[s["netlist"]].netlist.num_gates * s["stim"].num_cycles for s in specs)
     reqs = [serve.Request.from_spec(s) for s in specs]
-    opts = dict(tile_items=args.tile)
+    opts = dict(tile_items=args.tile, items_per_thread=args.ipt)
     serve.run_batched(nets, reqs, keep_results=False, **opts)          # warm-up
     t_b = []
     for _ in range(args.steps):
@@ -287,9 +287,9 @@ def run_served_mode(args):
     work = sum(nets[s["netlist"]].netlist.num_gates * s["stim"].num_cycles for s in specs)
     # warm-up on a short prefix of the stream
     warm = [serve.Request.from_spec(s) for s in specs[:8]]
-    serve.run_served(nets, warm, keep_results=False, tile_items=args.tile)
+    serve.run_served(nets, warm, keep_results=False, tile_items=args.tile, items_per_thread=args.ipt)
     reqs = [serve.Request.from_spec(s) for s in specs]
-    mk, st = serve.run_served(nets, reqs, tile_items=args.tile)
+    mk, st = serve.run_served(nets, reqs, tile_items=args.tile, items_per_thread=args.ipt)
     served = [r.result for r in reqs]
     lat = serve.latency_summary(reqs)
     reqs_p = [serve.Request.from_spec(s) for s in specs]
@@ -314,7 +314,11 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--tile", type=int, default=256)
+    ap.add_argument("--tile", type=int, default=0, help="threads per block (0 with --ipt 0: autotuned)")
+    ap.add_argument("--ipt", type=int, default=0, help="consecutive windows per thread (0: autotuned)")
+    ap.add_argument("--cycles", type=int, default=0,
+                    help="cycles of the benchmark workload (0 = the full 10,000); smaller values "
+                         "only for profiler captures")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--ref-seconds", type=float, default=120.0,
                     help="total oracle seconds of the reference arm (split over its steps)")
@@ -346,11 +350,11 @@ def main():
     import paper_2203_06117_gb300 as gs
     gs.build()
     device = local
-    wl = gen.make_workload(WORKLOAD, seed=SEED)
+    wl = gen.make_workload(WORKLOAD, seed=SEED, num_cycles=args.cycles or None)
     G, C = wl.netlist.num_gates, wl.stim.num_cycles
     units = G * C
     sim = gs.Simulator(wl.netlist, wl.delays, wl.stim, device=device)
-    opts = dict(window_cycles=1, tile_items=args.tile, time_kernels=1)
+    opts = dict(window_cycles=1, tile_items=args.tile, items_per_thread=args.ipt, time_kernels=1)
     for _ in range(args.warmup):
         sim.simulate(**opts)
     dist_barrier(world)
@@ -383,7 +387,7 @@ def main():
         t = time.perf_counter()
         gs.gatspi_set_stimulus(sim.ctx, stim.num_cycles, stim.cycle_ps, stim.init, stim.edge_ptr,
                                stim.edge_time)
-        gs.gatspi_simulate(sim.ctx, window_cycles=1, tile_items=args.tile)
+        gs.gatspi_simulate(sim.ctx, window_cycles=1, tile_items=args.tile, items_per_thread=args.ipt)
         saif = sim.saif()
         if k:
             e2e_times.append(time.perf_counter() - t)
@@ -397,7 +401,8 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-        "config": _config(args),
+        "config": dict(_config(args), cycles=C, tile_threads=st["tile_threads"],
+                       items_per_thread=st["items_per_thread"]),
         "e2e": {"value": units * world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h)},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",

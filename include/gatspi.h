@@ -67,13 +67,16 @@ typedef struct gatspi_opts {
   int32_t batch_windows; /* windows resident on the device at once; 0 = all
                             that fit in the arena (halved on overflow) */
   int32_t tile_items;    /* threads per block of the propagation kernel:
-                            128, 256 or 512; 0 = 256 */
+                            128, 256 or 512 (0 with items_per_thread 0:
+                            autotuned -- every variant is timed on a sample
+                            of the stimulus at the first call for a netlist
+                            and the fastest is kept; 0 otherwise: 256) */
   int32_t time_kernels;  /* 1 = time every propagation launch with CUDA
                             events on the library's stream (read back with
                             gatspi_get_stats) */
   int32_t items_per_thread; /* consecutive windows of one gate per thread:
                                1, 2, 4 or 8 (at most 4 with 512 threads);
-                               0 = 4 */
+                               0 = autotuned (see tile_items) or 4 */
   int32_t reserved[3];   /* must be 0 */
 } gatspi_opts;
 
@@ -96,6 +99,8 @@ typedef struct gatspi_stats {
   int32_t windows;         /* windows simulated */
   int32_t batch_windows;   /* windows per batch actually used */
   int32_t levels;          /* logic depth D */
+  int32_t tile_threads;    /* launch shape used: threads per block ... */
+  int32_t items_per_thread; /* ... and consecutive windows per thread */
 } gatspi_stats;
 
 /*

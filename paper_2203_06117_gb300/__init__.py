@@ -107,7 +107,8 @@ class gatspi_stats(ctypes.Structure):
                 ("prop_launches", ctypes.c_int64), ("items", ctypes.c_int64),
                 ("edges", ctypes.c_int64), ("algo_bytes", ctypes.c_int64),
                 ("batches", ctypes.c_int32), ("windows", ctypes.c_int32),
-                ("batch_windows", ctypes.c_int32), ("levels", ctypes.c_int32)]
+                ("batch_windows", ctypes.c_int32), ("levels", ctypes.c_int32),
+                ("tile_threads", ctypes.c_int32), ("items_per_thread", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

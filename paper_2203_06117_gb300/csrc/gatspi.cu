@@ -83,6 +83,8 @@ struct gatspi_ctx {
 
   // last simulation
   int32_t W = 1, batch_w0 = 0, batch_nw = 0, n_windows = 0, tile = 256;
+  int32_t window_limit = 0;          // >0: simulate only the first windows (autotuning)
+  int32_t tuned_nt = 0, tuned_ipt = 0;  // autotuned launch shape for this netlist
   gatspi_stats stats{};
   std::vector<cudaEvent_t> ev;
 };
@@ -242,6 +244,7 @@ int gatspi_load_netlist(gatspi_ctx* ctx, int32_t num_inputs, int32_t num_gates,
   if (!why.empty()) return fail(ctx, GATSPI_EINVAL, why);
   CK(cudaSetDevice(ctx->device));
   ctx->have_netlist = ctx->have_delays = ctx->have_stim = ctx->have_result = false;
+  ctx->tuned_nt = ctx->tuned_ipt = 0;
   free_netlist(ctx);
   ctx->I = r.I; ctx->G = r.G; ctx->N = r.N; ctx->P = r.P; ctx->D = r.D;
   ctx->gate_ext = std::move(r.gate_ext);
@@ -340,8 +343,11 @@ int gatspi_set_stimulus(gatspi_ctx* ctx, int32_t num_cycles, int32_t cycle_ps, c
   return GATSPI_OK;
 }
 
-int gatspi_simulate(gatspi_ctx* ctx, const gatspi_opts* opts) {
-  if (!ctx) return GATSPI_EINVAL;
+}  // extern "C"
+
+namespace {
+
+int simulate_impl(gatspi_ctx* ctx, const gatspi_opts* opts) {
   if (!ctx->have_netlist || !ctx->have_delays || !ctx->have_stim)
     return fail(ctx, GATSPI_ESTATE, "load a netlist, its delays and a stimulus first");
   const auto t_start = std::chrono::steady_clock::now();
@@ -364,7 +370,8 @@ int gatspi_simulate(gatspi_ctx* ctx, const gatspi_opts* opts) {
   if (!gatspi_host::horizon_fits(W, ctx->C, ctx->L, ctx->D, ctx->max_gate_delay, ctx->max_wire_delay,
                                  ctx->max_edit))
     return fail(ctx, GATSPI_EINVAL, "window length plus path delays could overflow int32 ps");
-  const int32_t n_windows = (ctx->C + W - 1) / W;
+  int32_t n_windows = (ctx->C + W - 1) / W;
+  if (ctx->window_limit > 0) n_windows = std::min(n_windows, ctx->window_limit);
   int32_t NW = o.batch_windows ? std::min(o.batch_windows, n_windows) : n_windows;
   // per-level item count must fit int32
   int64_t widest = ctx->I;
@@ -531,9 +538,69 @@ int gatspi_simulate(gatspi_ctx* ctx, const gatspi_opts* opts) {
     st.algo_bytes = b;
   }
   st.wall_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
+  st.tile_threads = nt;
+  st.items_per_thread = ipt;
   ctx->stats = st;
   ctx->have_result = true;
   return GATSPI_OK;
+}
+
+// Pick the launch shape (threads per block x consecutive windows per
+// thread) by timing every compiled variant on the first windows of the
+// loaded stimulus (about 10^8 (gate, window) items); cached per netlist.
+int autotune(gatspi_ctx* ctx, const gatspi_opts& base) {
+  static const int kVariants[][2] = {{256, 1}, {256, 2}, {256, 4}, {256, 8}, {128, 4},
+                                     {128, 8}, {512, 1}, {512, 2}, {512, 4}};
+  const int32_t W = base.window_cycles ? base.window_cycles : 1;
+  const int32_t n_windows = (ctx->C + W - 1) / W;
+  const int64_t want = (int64_t)1e8 / std::max<int64_t>(ctx->N, 1);
+  ctx->window_limit = (int32_t)std::max<int64_t>(1, std::min<int64_t>(want, n_windows));
+  double best = 1e300;
+  int bn = 256, bi = 4, rc = GATSPI_OK;
+  for (const auto& v : kVariants) {
+    gatspi_opts o = base;
+    o.tile_items = v[0];
+    o.items_per_thread = v[1];
+    o.time_kernels = 1;
+    double ms = 0;
+    for (int rep = 0; rep < 2 && rc == GATSPI_OK; ++rep) {
+      rc = simulate_impl(ctx, &o);
+      ms = ctx->stats.prop_ms;
+    }
+    if (rc != GATSPI_OK) break;
+    if (ms < best) {
+      best = ms;
+      bn = v[0];
+      bi = v[1];
+    }
+  }
+  ctx->window_limit = 0;
+  ctx->have_result = false;
+  if (rc != GATSPI_OK) return rc;
+  ctx->tuned_nt = bn;
+  ctx->tuned_ipt = bi;
+  return GATSPI_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int gatspi_simulate(gatspi_ctx* ctx, const gatspi_opts* opts) {
+  if (!ctx) return GATSPI_EINVAL;
+  if (!ctx->have_netlist || !ctx->have_delays || !ctx->have_stim)
+    return fail(ctx, GATSPI_ESTATE, "load a netlist, its delays and a stimulus first");
+  gatspi_opts o{};
+  if (opts) o = *opts;
+  if (o.tile_items == 0 && o.items_per_thread == 0) {
+    if (!ctx->tuned_nt) {
+      const int rc = autotune(ctx, o);
+      if (rc) return rc;
+    }
+    o.tile_items = ctx->tuned_nt;
+    o.items_per_thread = ctx->tuned_ipt;
+  }
+  return simulate_impl(ctx, &o);
 }
 
 int gatspi_saif(gatspi_ctx* ctx, int64_t* t0, int64_t* t1, int64_t* tc) {
