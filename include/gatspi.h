@@ -297,6 +297,84 @@ int gatspi_engine_release(gatspi_engine* eng, int64_t job_id);
 
 int gatspi_engine_get_stats(gatspi_engine* eng, gatspi_engine_stats* out);
 
+/* ------------------------------------------------------------------------
+ * Allocation-free level propagation.  (The paper has no counterpart: this
+ * is an interface for embedding, not part of the method.)
+ *
+ * Some callers cannot call cudaMalloc: code whose device memory comes from
+ * a framework or pool it does not own, code that must not synchronize the
+ * device (allocation and release may), and code that reserved all memory up
+ * front and must not fail for lack of it mid-run.  This entry point runs the
+ * propagation kernel for ONE logic level of ONE job into buffers the caller
+ * allocated, and allocates nothing itself: the kernel's only extra memory
+ * (one look-back word per tile and a tile counter) is a fixed array of
+ * GATSPI_NOALLOC_MAX_TILES + 32 words (about 512 KB) held by every device
+ * that loads the library until the process exits.
+ *
+ * Buffer layout (the one gatspi_simulate uses internally), for a batch of
+ * num_windows windows starting at window first_window:
+ *   - nets 0..I-1 are inputs, then gates in level order: all gates of level
+ *     l are contiguous, gate_begin..gate_end-1 of this call are exactly the
+ *     gates of `level` (0-based gate indices), and gate g drives net I+g;
+ *     fanin_ptr/fanin_net/lut/gate_delay/wire_delay are as in
+ *     gatspi_load_netlist / gatspi_load_delays (fanin nets in this order);
+ *     net_level[n] is the level of net n (inputs 0);
+ *   - init[n*NW + w] (uint8): value of net n at the start of window w;
+ *   - off[n*NW + w + level(n)] (int32): first edge of (n, w) relative to
+ *     lvl_base[level(n)], with one extra slot after each level's last
+ *     record that closes it (so off has N*NW + D + 1 entries);
+ *   - times[lvl_base[l] + off ...] (int32): window-relative edge times,
+ *     `capacity` elements in all; lvl_base (int64, D+2 entries);
+ *   - saif_t1 / saif_tc (uint64 [N]): time at 1 and toggle count, added to;
+ *   - status (int32): error bits are ORed in (1 capacity, 2 wait timeout,
+ *     4 corrupt record, 8 offset overflow); clear it before the first call.
+ * The call reads levels < `level` and lvl_base[level]; it writes the records
+ * and edges of `level`, lvl_base[level + 1], and the SAIF of its gates.
+ *
+ * The work is queued on `stream` (NULL = default stream) and not waited
+ * for.  The first call on a device looks up the scratch array's device
+ * address; make that first call before any stream capture on the device.
+ * Every call on a device shares the scratch array, which keeps the last
+ * call's contents (each call clears the part it uses first): calls that may
+ * overlap on the GPU -- on different streams without ordering -- race and
+ * give wrong results.  Levels of one job must run in order anyway.
+ * Errors: EINVAL (null pointer, bad range), ECAPACITY (more than
+ * GATSPI_NOALLOC_MAX_TILES * 1024 (gate, window) items in the level: use
+ * fewer windows per call), ECUDA.  A message is written to err/err_len
+ * when given.
+ * ---------------------------------------------------------------------- */
+#define GATSPI_NOALLOC_MAX_TILES 65536
+
+typedef struct gatspi_level_args {
+  const int32_t* fanin_ptr;
+  const int32_t* fanin_net;
+  const uint16_t* lut;
+  const int32_t* gate_delay;
+  const int32_t* wire_delay;
+  const int32_t* net_level;
+  uint8_t* init;
+  int32_t* off;
+  int32_t* times;
+  int64_t* lvl_base;
+  int64_t capacity;
+  uint64_t* saif_t1;
+  uint64_t* saif_tc;
+  int32_t* status;
+  int32_t num_inputs;
+  int32_t level;
+  int32_t gate_begin;
+  int32_t gate_end;
+  int32_t num_windows;
+  int32_t first_window;
+  int32_t window_cycles;
+  int32_t num_cycles;
+  int32_t cycle_ps;
+  int32_t err_len;
+  char* err;
+} gatspi_level_args;
+
+int gatspi_propagate_level_noalloc(const gatspi_level_args* args, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -27,7 +27,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(_HERE)
 LIB_PATH = os.path.join(_HERE, "_build", "libgatspi.so")
 INCLUDE = os.path.join(ROOT, "include")
-SOURCES = [os.path.join(_HERE, "csrc", f) for f in ("gatspi.cu", "engine.cu")]
+SOURCES = [os.path.join(_HERE, "csrc", f) for f in ("gatspi.cu", "engine.cu", "noalloc.cu")]
 DEPS = SOURCES + [os.path.join(_HERE, "csrc", f) for f in ("kernels.cuh", "host_common.h")] + \
     [os.path.join(INCLUDE, "gatspi.h")]
 
@@ -45,7 +45,7 @@ EXPORTS = ["gatspi_create", "gatspi_destroy", "gatspi_last_error", "gatspi_load_
            "gatspi_engine_create", "gatspi_engine_destroy", "gatspi_engine_last_error",
            "gatspi_engine_add_netlist", "gatspi_engine_submit", "gatspi_engine_step",
            "gatspi_engine_drain", "gatspi_engine_poll", "gatspi_engine_release",
-           "gatspi_engine_get_stats"]
+           "gatspi_engine_get_stats", "gatspi_propagate_level_noalloc"]
 
 JOB_QUEUED, JOB_RUNNING, JOB_DONE, JOB_FAILED = 0, 1, 2, 3
 
@@ -100,6 +100,19 @@ class gatspi_engine_stats(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class gatspi_level_args(ctypes.Structure):
+    """Arguments of gatspi_propagate_level_noalloc (device pointers as ints)."""
+    _fields_ = [(n, ctypes.c_void_p) for n in ("fanin_ptr", "fanin_net", "lut", "gate_delay",
+                                                 "wire_delay", "net_level", "init", "off", "times",
+                                                 "lvl_base")] + \
+               [("capacity", ctypes.c_int64)] + \
+               [(n, ctypes.c_void_p) for n in ("saif_t1", "saif_tc", "status")] + \
+               [(n, ctypes.c_int32) for n in ("num_inputs", "level", "gate_begin", "gate_end",
+                                               "num_windows", "first_window", "window_cycles",
+                                               "num_cycles", "cycle_ps", "err_len")] + \
+               [("err", ctypes.c_char_p)]
+
+
 class gatspi_stats(ctypes.Structure):
     _fields_ = [("prop_ms", ctypes.c_double), ("input_ms", ctypes.c_double),
                 ("wall_ms", ctypes.c_double), ("device_ms", ctypes.c_double),
@@ -152,6 +165,7 @@ def lib():
         L.gatspi_engine_poll.argtypes = [vp, i64, ctypes.POINTER(ctypes.c_int32), vp, vp, vp]
         L.gatspi_engine_release.argtypes = [vp, i64]
         L.gatspi_engine_get_stats.argtypes = [vp, ctypes.POINTER(gatspi_engine_stats)]
+        L.gatspi_propagate_level_noalloc.argtypes = [ctypes.POINTER(gatspi_level_args), vp]
         for name in EXPORTS:
             if not name.endswith("last_error"):
                 getattr(L, name).restype = ctypes.c_int

@@ -1,0 +1,122 @@
+// Level propagation into caller-owned buffers without any device allocation
+// (gatspi_propagate_level_noalloc in include/gatspi.h).
+//
+// Some callers cannot call cudaMalloc: code whose device memory is handed
+// out by a framework or a pool it does not own, code that must not
+// synchronize the device (cudaMalloc and cudaFree may), or code that has
+// reserved all memory up front and must not fail for lack of it mid-run.
+// They allocate the netlist, delay and waveform buffers themselves and pass
+// them in.  The only memory the propagation kernel needs beyond those
+// buffers -- one look-back word per tile of the level and a tile counter --
+// lives in a fixed array in this file, so this entry point never allocates.
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cstdio>
+
+#include "gatspi.h"
+#include "kernels.cuh"
+
+using namespace gatspi_dev;
+
+namespace {
+
+constexpr int kNoAllocThreads = 256;
+constexpr int kNoAllocItemsPerThread = 4;
+constexpr int kNoAllocTileItems = kNoAllocThreads * kNoAllocItemsPerThread;
+constexpr int kMaxDevices = 64;
+
+}  // namespace
+
+// One look-back word per tile (at most GATSPI_NOALLOC_MAX_TILES tiles in a
+// level), then the launch's tile counter.  Shared by every call on a
+// device; each call clears the part it uses before its kernel runs.
+static __device__ __align__(256) unsigned long long
+    g_noalloc_scratch[GATSPI_NOALLOC_MAX_TILES + 32];
+
+namespace {
+
+// Device address of g_noalloc_scratch, looked up once per device.  In host
+// code the array's name only stands in for the device symbol, so the
+// address must come from cudaGetSymbolAddress with the device current.
+std::atomic<int> g_state[kMaxDevices];  // 0 = unknown, 1 = busy, 2 = ready
+unsigned long long* g_addr[kMaxDevices];
+
+int scratch_address(int device, unsigned long long** out) {
+  if (device < 0 || device >= kMaxDevices) return GATSPI_EINVAL;
+  for (;;) {
+    int s = g_state[device].load(std::memory_order_acquire);
+    if (s == 2) {
+      *out = g_addr[device];
+      return GATSPI_OK;
+    }
+    if (s == 0 && g_state[device].compare_exchange_strong(s, 1)) {
+      void* p = nullptr;
+      const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+      if (e != cudaSuccess || !p) {
+        g_state[device].store(0, std::memory_order_release);
+        return GATSPI_ECUDA;
+      }
+      g_addr[device] = (unsigned long long*)p;
+      g_state[device].store(2, std::memory_order_release);
+      *out = g_addr[device];
+      return GATSPI_OK;
+    }
+  }
+}
+
+int say(const gatspi_level_args* a, int code, const char* msg) {
+  if (a && a->err && a->err_len > 0) std::snprintf(a->err, (size_t)a->err_len, "%s", msg);
+  return code;
+}
+
+}  // namespace
+
+extern "C" int gatspi_propagate_level_noalloc(const gatspi_level_args* a, void* stream) {
+  if (!a) return GATSPI_EINVAL;
+  if (a->err && a->err_len > 0) a->err[0] = 0;
+  if (!a->fanin_ptr || !a->fanin_net || !a->lut || !a->gate_delay || !a->wire_delay || !a->net_level ||
+      !a->init || !a->off || !a->times || !a->lvl_base || !a->saif_t1 || !a->saif_tc || !a->status)
+    return say(a, GATSPI_EINVAL, "a device pointer is null");
+  if (a->num_inputs < 1 || a->level < 1 || a->gate_begin < 0 || a->gate_end <= a->gate_begin ||
+      a->num_windows < 1 || a->first_window < 0 || a->window_cycles < 1 || a->num_cycles < 1 ||
+      a->cycle_ps < 1 || a->capacity < 0)
+    return say(a, GATSPI_EINVAL, "bad level, gate range, window or cycle argument");
+  const long long items = (long long)(a->gate_end - a->gate_begin) * a->num_windows;
+  const long long tiles = (items + kNoAllocTileItems - 1) / kNoAllocTileItems;
+  if (items > 0x7fffffffll || tiles > GATSPI_NOALLOC_MAX_TILES)
+    return say(a, GATSPI_ECAPACITY,
+               "level too large for the fixed look-back scratch: more than "
+               "GATSPI_NOALLOC_MAX_TILES * 1024 (gate, window) items; use fewer windows per call");
+  int device = 0;
+  if (cudaGetDevice(&device) != cudaSuccess) return say(a, GATSPI_ECUDA, "cudaGetDevice failed");
+  unsigned long long* scratch = nullptr;
+  int rc = scratch_address(device, &scratch);
+  if (rc) return say(a, rc, "cudaGetSymbolAddress of the look-back scratch failed");
+  cudaStream_t s = (cudaStream_t)stream;
+  // the look-back words of this level and the tile counter must start at 0
+  if (cudaMemsetAsync(scratch, 0, sizeof(unsigned long long) * (size_t)tiles, s) != cudaSuccess ||
+      cudaMemsetAsync(scratch + GATSPI_NOALLOC_MAX_TILES, 0, sizeof(unsigned long long), s) != cudaSuccess)
+    return say(a, GATSPI_ECUDA, "clearing the look-back scratch failed");
+  PropParams p{};
+  JobView& j = p.job;
+  j.fanin_ptr = a->fanin_ptr; j.fanin_net = a->fanin_net; j.lut = a->lut;
+  j.gate_delay = a->gate_delay; j.wire_delay = a->wire_delay; j.net_level = a->net_level;
+  j.gate_delta = nullptr;
+  j.init = a->init; j.off = a->off; j.times = a->times; j.lvl_base = (long long*)a->lvl_base;
+  j.capacity = a->capacity;
+  j.saif_t1 = (unsigned long long*)a->saif_t1; j.saif_tc = (unsigned long long*)a->saif_tc;
+  j.status = a->status;
+  j.I = a->num_inputs; j.NW = a->num_windows; j.w0 = a->first_window; j.W = a->window_cycles;
+  j.C = a->num_cycles; j.L = a->cycle_ps;
+  p.seg.tile_state = scratch;
+  p.seg.level = a->level;
+  p.seg.gate_begin = a->gate_begin;
+  p.seg.net_end = a->num_inputs + a->gate_end;
+  p.seg.n_items = (int32_t)items;
+  p.seg.n_tiles = (int32_t)tiles;
+  p.tile_counter = (int32_t*)(scratch + GATSPI_NOALLOC_MAX_TILES);
+  propagate_kernel<kNoAllocThreads, kNoAllocItemsPerThread><<<(unsigned)tiles, kNoAllocThreads, 0, s>>>(p);
+  if (cudaGetLastError() != cudaSuccess) return say(a, GATSPI_ECUDA, "kernel launch failed");
+  return GATSPI_OK;
+}
