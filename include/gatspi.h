@@ -56,7 +56,7 @@ extern "C" {
 #define GATSPI_ENOMEM (-2)    /* device or host allocation failed */
 #define GATSPI_ECAPACITY (-3) /* waveforms do not fit, even one window per batch */
 #define GATSPI_ECUDA (-4)     /* a CUDA call failed */
-#define GATSPI_ETIMEOUT (-5)  /* a bounded device-side wait ran out */
+#define GATSPI_ETIMEOUT (-5)  /* a bounded device-side wait ran out (no kernel waits today) */
 #define GATSPI_ESTATE (-6)    /* call out of order */
 
 typedef struct gatspi_ctx gatspi_ctx;
@@ -169,8 +169,8 @@ int gatspi_set_stimulus(gatspi_ctx* ctx, int32_t num_cycles, int32_t cycle_ps,
 
 /*
  * Simulate every window (Algorithm 1 for every gate and window, level by
- * level; output storage sized by a scan over the produced edge counts,
- * Section 3) and accumulate SAIF.  Synchronous.  `opts` may be NULL.
+ * level; output storage claimed from the produced edge counts in the
+ * same pass, where Section 3 counts, scans and stores in two) and accumulate SAIF.  Synchronous.  `opts` may be NULL.
  * Errors: ESTATE, EINVAL (options, or times that could overflow int32),
  * ECAPACITY, ETIMEOUT, ECUDA.
  */
@@ -211,7 +211,7 @@ int gatspi_get_stats(gatspi_ctx* ctx, gatspi_stats* out);
  * part, whatever its netlist or level (continuous batching).  A part that
  * finishes frees its memory at once, so waiting parts join mid-flight.
  * Each part's results are bit-identical to a plain gatspi_simulate of the
- * same job: parts never share look-back chains or waveform stores.
+ * same job: parts never share counters or waveform stores.
  * The paper runs one design at a time (Section 3); its glitch-optimization
  * loop (Section 4) re-simulates after delay edits, which is the workload
  * the edits below serve.
@@ -307,27 +307,29 @@ int gatspi_engine_get_stats(gatspi_engine* eng, gatspi_engine_stats* out);
  * front and must not fail for lack of it mid-run.  This entry point runs the
  * propagation kernel for ONE logic level of ONE job into buffers the caller
  * allocated, and allocates nothing itself: the kernel's only extra memory
- * (one look-back word per tile and a tile counter) is a fixed array of
- * GATSPI_NOALLOC_MAX_TILES + 32 words (about 512 KB) held by every device
+ * (the level's counter of edges allocated and tiles done, and the launch's
+ * tile counter) is a fixed array of 32 words (256 bytes) held by every device
  * that loads the library until the process exits.
  *
  * Buffer layout (the one gatspi_simulate uses internally), for a batch of
- * num_windows windows starting at window first_window:
+ * NW = num_windows windows starting at window first_window:
  *   - nets 0..I-1 are inputs, then gates in level order: all gates of level
  *     l are contiguous, gate_begin..gate_end-1 of this call are exactly the
  *     gates of `level` (0-based gate indices), and gate g drives net I+g;
  *     fanin_ptr/fanin_net/lut/gate_delay/wire_delay are as in
  *     gatspi_load_netlist / gatspi_load_delays (fanin nets in this order);
  *     net_level[n] is the level of net n (inputs 0);
- *   - init[n*NW + w] (uint8): value of net n at the start of window w;
- *   - off[n*NW + w + level(n)] (int32): first edge of (n, w) relative to
- *     lvl_base[level(n)], with one extra slot after each level's last
- *     record that closes it (so off has N*NW + D + 1 entries);
- *   - times[lvl_base[l] + off ...] (int32): window-relative edge times,
- *     `capacity` elements in all; lvl_base (int64, D+2 entries);
+ *   - rstart[n*NW + w] (int32): first edge of (net n, window w), relative
+ *     to lvl_base[level(n)];
+ *   - rmeta[n*NW + w] (uint16): bit 15 the value of net n at the start of
+ *     window w, bits 0-14 its number of edges in the window;
+ *   - times[lvl_base[l] + rstart ...] (int32): window-relative edge times,
+ *     `capacity` elements in all; lvl_base (int64, D+2 entries).  A level's
+ *     records may appear in any order inside its range of times;
  *   - saif_t1 / saif_tc (uint64 [N]): time at 1 and toggle count, added to;
  *   - status (int32): error bits are ORed in (1 capacity, 2 wait timeout,
- *     4 corrupt record, 8 offset overflow); clear it before the first call.
+ *     4 corrupt record, 8 offset overflow: a level's edges beyond int32 or
+ *     a record beyond 32767 edges); clear it before the first call.
  * The call reads levels < `level` and lvl_base[level]; it writes the records
  * and edges of `level`, lvl_base[level + 1], and the SAIF of its gates.
  *
@@ -335,15 +337,14 @@ int gatspi_engine_get_stats(gatspi_engine* eng, gatspi_engine_stats* out);
  * for.  The first call on a device looks up the scratch array's device
  * address; make that first call before any stream capture on the device.
  * Every call on a device shares the scratch array, which keeps the last
- * call's contents (each call clears the part it uses first): calls that may
- * overlap on the GPU -- on different streams without ordering -- race and
- * give wrong results.  Levels of one job must run in order anyway.
+ * call's contents (each call clears it first): calls that may overlap on
+ * the GPU -- on different streams without ordering -- race and give wrong
+ * results.  Levels of one job must run in order anyway.
  * Errors: EINVAL (null pointer, bad range), ECAPACITY (more than
- * GATSPI_NOALLOC_MAX_TILES * 1024 (gate, window) items in the level: use
- * fewer windows per call), ECUDA.  A message is written to err/err_len
- * when given.
+ * GATSPI_NOALLOC_MAX_ITEMS (gate, window) items in the level: use fewer
+ * windows per call), ECUDA.  A message is written to err/err_len when given.
  * ---------------------------------------------------------------------- */
-#define GATSPI_NOALLOC_MAX_TILES 65536
+#define GATSPI_NOALLOC_MAX_ITEMS 2147418112LL /* 0x7fff0000 */
 
 typedef struct gatspi_level_args {
   const int32_t* fanin_ptr;
@@ -352,8 +353,8 @@ typedef struct gatspi_level_args {
   const int32_t* gate_delay;
   const int32_t* wire_delay;
   const int32_t* net_level;
-  uint8_t* init;
-  int32_t* off;
+  int32_t* rstart;
+  uint16_t* rmeta;
   int32_t* times;
   int64_t* lvl_base;
   int64_t capacity;

@@ -65,17 +65,16 @@ struct EPart {
   int64_t edge_hint = 0;
   char* mem = nullptr;
   size_t bytes = 0;
-  uint8_t* init = nullptr;
-  int32_t* off = nullptr;
+  int32_t* rstart = nullptr;
+  uint16_t* rmeta = nullptr;
   int32_t* times = nullptr;
   long long cap = 0;
   long long* lvl_base = nullptr;
-  unsigned long long* tiles = nullptr;
+  unsigned long long* counters = nullptr;  // per level: packed tiles done / edges allocated
   int32_t* status = nullptr;
   unsigned long long* t1 = nullptr;
   unsigned long long* tc = nullptr;
   size_t zero_off = 0, zero_bytes = 0;
-  std::vector<int64_t> tile_base;
   int32_t slot = -1;  // pinned result slot
   cudaEvent_t ev = nullptr;
 };
@@ -89,7 +88,7 @@ struct gatspi_engine {
   size_t budget = 0, in_use = 0;
   gatspi_engine_opts opts{};
   int nt = 256, ipt = 4;
-  int tile = 1024;  // items per block
+  int tile = 128;  // items per warp tile (linear tiling)
   std::vector<std::unique_ptr<ENetlist>> nets;
   std::map<int64_t, std::unique_ptr<EJob>> jobs;
   int64_t next_job = 1;
@@ -156,32 +155,25 @@ void dfree_async(T*& p, cudaStream_t s) {
 }
 
 // Lay out one part's device memory; returns the total bytes.
-size_t part_layout(const ENetlist& nl, EPart& p, int tile, char* base) {
+size_t part_layout(const ENetlist& nl, EPart& p, char* base) {
   const int64_t N = nl.r.N, D = nl.r.D, NW = p.nw;
   int64_t o = 0;
-  const int64_t o_init = o; o = align_up(o + N * NW);
-  const int64_t o_off = o; o = align_up(o + (N * NW + D + 2) * 4);
+  const int64_t o_start = o; o = align_up(o + N * NW * 4);
+  const int64_t o_meta = o; o = align_up(o + N * NW * 2);
   const int64_t o_lvl = o; o = align_up(o + (D + 2) * 8);
-  // zeroed region: look-back words, status, part SAIF
+  // zeroed region: level counters, status, part SAIF
   const int64_t o_zero = o;
-  p.tile_base.assign(D + 2, 0);
-  int64_t tiles = 0;
-  for (int32_t l = 1; l <= D; ++l) {
-    p.tile_base[l] = tiles;
-    const int64_t items = (int64_t)(nl.r.lvl_gate_begin[l + 1] - nl.r.lvl_gate_begin[l]) * NW;
-    tiles += (items + tile - 1) / tile;
-  }
-  const int64_t o_tiles = o; o = align_up(o + tiles * 8);
+  const int64_t o_cnt = o; o = align_up(o + (D + 2) * 8);
   const int64_t o_status = o; o = align_up(o + 8);
   const int64_t o_t1 = o; o = align_up(o + N * 8);
   const int64_t o_tc = o; o = align_up(o + N * 8);
   const int64_t zero_end = o;
   const int64_t o_times = o; o = align_up(o + p.edge_hint * 4);
   if (base) {
-    p.init = (uint8_t*)(base + o_init);
-    p.off = (int32_t*)(base + o_off);
+    p.rstart = (int32_t*)(base + o_start);
+    p.rmeta = (uint16_t*)(base + o_meta);
     p.lvl_base = (long long*)(base + o_lvl);
-    p.tiles = (unsigned long long*)(base + o_tiles);
+    p.counters = (unsigned long long*)(base + o_cnt);
     p.status = (int32_t*)(base + o_status);
     p.t1 = (unsigned long long*)(base + o_t1);
     p.tc = (unsigned long long*)(base + o_tc);
@@ -198,7 +190,7 @@ JobView make_view(const ENetlist& nl, const EJob& j, const EPart& p) {
   v.fanin_ptr = nl.d_fanin_ptr; v.fanin_net = nl.d_fanin_net; v.lut = nl.d_lut;
   v.gate_delay = nl.d_gate_delay; v.wire_delay = nl.d_wire_delay; v.net_level = nl.d_net_level;
   v.gate_delta = j.d_gate_delta;
-  v.init = p.init; v.off = p.off; v.times = p.times; v.lvl_base = p.lvl_base; v.capacity = p.cap;
+  v.rstart = p.rstart; v.rmeta = p.rmeta; v.times = p.times; v.lvl_base = p.lvl_base; v.capacity = p.cap;
   v.saif_t1 = p.t1; v.saif_tc = p.tc; v.status = p.status;
   v.I = nl.r.I; v.NW = p.nw; v.w0 = p.w0; v.W = j.W; v.C = j.C; v.L = j.L;
   return v;
@@ -281,7 +273,7 @@ int retire(gatspi_engine* eng, bool wait_one) {
         j.parts_total++;
         eng->queued.push_front(std::move(b));
       } else if (res.status & kStOffset) {
-        rc = fail_job(eng, j, GATSPI_ECAPACITY, "one window's edges exceed the int32 offset range");
+        rc = fail_job(eng, j, GATSPI_ECAPACITY, "a net has more than 32767 edges in one window, or one window's edges exceed the int32 offset range");
       } else {
         again->w0 = p.w0; again->nw = p.nw;
         again->edge_hint = std::max<int64_t>(2 * p.edge_hint, res.edges + 1024);
@@ -335,7 +327,7 @@ int gatspi_engine_create(gatspi_engine** out, int device, size_t arena_bytes, co
   eng->opts = o;
   eng->nt = nt;
   eng->ipt = ipt;
-  eng->tile = nt * ipt;
+  eng->tile = tile_items_of(ipt);
   if (!eng->opts.max_active) eng->opts.max_active = 1024;
   if (!eng->opts.part_items) eng->opts.part_items = 1ll << 28;
   if (cudaSetDevice(device) != cudaSuccess ||
@@ -475,7 +467,7 @@ int gatspi_engine_submit(gatspi_engine* eng, int32_t netlist_id, int32_t num_cyc
   for (int32_t l = 1; l <= nl.r.D; ++l)
     widest = std::max<int64_t>(widest, nl.r.lvl_gate_begin[l + 1] - nl.r.lvl_gate_begin[l]);
   int64_t per = std::max<int64_t>(1, eng->opts.part_items / std::max<int64_t>(nl.r.N, 1));
-  per = std::min<int64_t>(per, 0x7ffffff0ll / widest);
+  per = std::min<int64_t>(per, 0x7fff0000ll / widest);
   per = std::max<int64_t>(per, 1);
   for (int32_t w0 = 0; w0 < j->n_windows; w0 += (int32_t)per) {
     std::unique_ptr<EPart> p(new EPart());
@@ -519,7 +511,7 @@ int gatspi_engine_step(gatspi_engine* eng, int32_t* active_out, int32_t* queued_
         l0 += j.edge_ptr[(size_t)i * j.C + c1] - j.edge_ptr[(size_t)i * j.C + c0];
       p.edge_hint = l0 + (int64_t)(nl.edges_per_item * (double)nl.r.G * p.nw * 1.25) + 4096;
     }
-    const size_t bytes = part_layout(nl, p, eng->tile, nullptr);
+    const size_t bytes = part_layout(nl, p, nullptr);
     if (bytes > eng->budget) {
       if (p.nw > 1) {  // split and retry
         std::unique_ptr<EPart> b(new EPart());
@@ -543,7 +535,7 @@ int gatspi_engine_step(gatspi_engine* eng, int32_t* active_out, int32_t* queued_
     eng->queued.pop_front();
     own->mem = (char*)mem;
     own->bytes = bytes;
-    part_layout(nl, *own, eng->tile, own->mem);
+    part_layout(nl, *own, own->mem);
     eng->in_use += bytes;
     eng->stats.bytes_peak = std::max<int64_t>(eng->stats.bytes_peak, (int64_t)eng->in_use);
     ECK(cudaMemsetAsync(own->mem + own->zero_off, 0, own->zero_bytes, eng->stream));
@@ -593,12 +585,12 @@ int gatspi_engine_step(gatspi_engine* eng, int32_t* active_out, int32_t* queued_
     ENetlist& nl = *eng->nets[j.net];
     const int32_t l = p->level;
     MultiSeg s{};
-    s.seg.tile_state = p->tiles + p->tile_base[l];
+    s.seg.counters = p->counters + l;
     s.seg.level = l;
     s.seg.gate_begin = nl.r.lvl_gate_begin[l];
-    s.seg.net_end = nl.r.I + nl.r.lvl_gate_begin[l + 1];
     s.seg.n_items = (nl.r.lvl_gate_begin[l + 1] - nl.r.lvl_gate_begin[l]) * p->nw;
-    s.seg.n_tiles = (s.seg.n_items + eng->tile - 1) / eng->tile;
+    s.seg.n_tiles = (int32_t)level_tiles(nl.r.lvl_gate_begin[l + 1] - nl.r.lvl_gate_begin[l], p->nw, eng->ipt);
+    s.seg.wide = wide_tiling(p->nw, eng->ipt) ? 1 : 0;
     s.job = (int32_t)views.size();
     s.tile_begin = (int32_t)tiles;
     tiles += s.seg.n_tiles;
@@ -620,8 +612,9 @@ int gatspi_engine_step(gatspi_engine* eng, int32_t* active_out, int32_t* queued_
     m.jobs = (const JobView*)(eng->d_stage + jobs_off);
     m.segs = (const MultiSeg*)(eng->d_stage + segs_off);
     m.n_segs = (int32_t)segs.size();
+    m.n_tiles = (int32_t)tiles;
     m.tile_counter = eng->d_counter;
-    MultiLaunch go{&m, (unsigned)tiles, eng->stream};
+    MultiLaunch go{&m, eng->stream};
     launch_variant(eng->nt, eng->ipt, go);
     ECK(cudaGetLastError());
     eng->stats.steps++;
@@ -634,8 +627,8 @@ int gatspi_engine_step(gatspi_engine* eng, int32_t* active_out, int32_t* queued_
     InputParams q{};
     q.edge_ptr = j.d_edge_ptr; q.edge_time = j.d_edge_time; q.init_in = j.d_init_in;
     q.in_prefix = (const long long*)(eng->d_stage + pre_off[k]);
-    q.init = p.init; q.off = p.off; q.times = p.times; q.saif_t1 = p.t1; q.saif_tc = p.tc;
-    q.lvl_base = p.lvl_base;
+    q.rstart = p.rstart; q.rmeta = p.rmeta; q.times = p.times; q.saif_t1 = p.t1; q.saif_tc = p.tc;
+    q.lvl_base = p.lvl_base; q.status = p.status;
     long long l0 = 0;
     const int32_t c0 = p.w0 * j.W, c1 = std::min((p.w0 + p.nw) * j.W, j.C);
     for (int32_t i = 0; i < nl.r.I; ++i)

@@ -71,15 +71,14 @@ struct gatspi_ctx {
   char* d_arena = nullptr;
   size_t arena_bytes = 0;
   int64_t times_cap_hint = 0;
-  uint8_t* d_init = nullptr;
-  int32_t* d_off = nullptr;
-  unsigned long long* d_tile_state = nullptr;
+  int32_t* d_rstart = nullptr;
+  uint16_t* d_rmeta = nullptr;
+  unsigned long long* d_counters = nullptr;  // per level: packed tiles done / edges allocated
   int32_t* d_tile_counter = nullptr;
   long long* d_lvl_base = nullptr;
   int32_t* d_times = nullptr;
   int64_t times_cap = 0;
-  size_t scratch_bytes = 0;  // tile states + counters (zeroed per batch)
-  std::vector<int64_t> tile_base;  // per level, offset into tile states
+  size_t scratch_bytes = 0;  // counters (zeroed per batch)
 
   // last simulation
   int32_t W = 1, batch_w0 = 0, batch_nw = 0, n_windows = 0, tile = 256;
@@ -135,31 +134,24 @@ void free_arena(gatspi_ctx* c) {
 }
 
 // Carve the arena for a batch of NW windows; returns false if it does not fit.
-bool plan_batch(gatspi_ctx* c, int32_t NW, int tile, size_t* need_fixed) {
+bool plan_batch(gatspi_ctx* c, int32_t NW, size_t* need_fixed) {
   const int64_t N = c->N;
   int64_t off = 0;
-  const int64_t o_init = off; off = align_up(off + N * NW);
-  const int64_t o_off = off; off = align_up(off + (N * NW + c->D + 2) * 4);
+  const int64_t o_start = off; off = align_up(off + N * NW * 4);
+  const int64_t o_meta = off; off = align_up(off + N * NW * 2);
   const int64_t o_lvl = off; off = align_up(off + (c->D + 2) * 8);
   const int64_t o_scr = off;
-  c->tile_base.assign(c->D + 2, 0);
-  int64_t tiles = 0;
-  for (int32_t l = 1; l <= c->D; ++l) {
-    c->tile_base[l] = tiles;
-    const int64_t items = (int64_t)(c->lvl_gate_begin[l + 1] - c->lvl_gate_begin[l]) * NW;
-    tiles += (items + tile - 1) / tile;
-  }
-  const int64_t o_cnt = align_up(o_scr + tiles * 8);
+  const int64_t o_cnt = align_up(o_scr + (int64_t)(c->D + 2) * 8);
   off = align_up(o_cnt + (c->D + 2) * 4);
   c->scratch_bytes = (size_t)(off - o_scr);
   const int64_t o_times = off;
   *need_fixed = (size_t)o_times;
   if ((size_t)o_times + 1024 * 4 > c->arena_bytes) return false;
   char* a = c->d_arena;
-  c->d_init = (uint8_t*)(a + o_init);
-  c->d_off = (int32_t*)(a + o_off);
+  c->d_rstart = (int32_t*)(a + o_start);
+  c->d_rmeta = (uint16_t*)(a + o_meta);
   c->d_lvl_base = (long long*)(a + o_lvl);
-  c->d_tile_state = (unsigned long long*)(a + o_scr);
+  c->d_counters = (unsigned long long*)(a + o_scr);
   c->d_tile_counter = (int32_t*)(a + o_cnt);
   c->d_times = (int32_t*)(a + o_times);
   c->times_cap = (int64_t)((c->arena_bytes - (size_t)o_times) / 4);
@@ -182,13 +174,10 @@ int ensure_arena(gatspi_ctx* ctx, size_t bytes) {
 }
 
 // Fixed bytes (everything but edge times) for NW windows.
-size_t fixed_bytes(const gatspi_ctx* c, int32_t NW, int tile) {
+size_t fixed_bytes(const gatspi_ctx* c, int32_t NW) {
   const int64_t N = c->N;
-  int64_t tiles = 0;
-  for (int32_t l = 1; l <= c->D; ++l)
-    tiles += ((int64_t)(c->lvl_gate_begin[l + 1] - c->lvl_gate_begin[l]) * NW + tile - 1) / tile;
-  return (size_t)(align_up(N * NW) + align_up((N * NW + c->D + 2) * 4) + align_up((c->D + 2) * 8) +
-                  align_up(tiles * 8) + align_up((c->D + 2) * 4) + 4096);
+  return (size_t)(align_up(N * NW * 4) + align_up(N * NW * 2) + align_up((c->D + 2) * 8) +
+                  align_up((int64_t)(c->D + 2) * 8) + align_up((c->D + 2) * 4) + 4096);
 }
 
 }  // namespace
@@ -364,7 +353,7 @@ int simulate_impl(gatspi_ctx* ctx, const gatspi_opts* opts) {
       (nt == 512 && ipt == 8))
     return fail(ctx, GATSPI_EINVAL, "tile_items must be 128, 256 or 512 and items_per_thread 1, 2, 4 or 8 "
                                     "(at most 4 with 512)");
-  const int tile = nt * ipt;  // items per block
+  const int tile = tile_items_of(ipt);  // items per warp tile
   if (o.batch_windows < 0) return fail(ctx, GATSPI_EINVAL, "batch_windows must be >= 0");
   // every time stays below 2^31: window length plus the longest path
   if (!gatspi_host::horizon_fits(W, ctx->C, ctx->L, ctx->D, ctx->max_gate_delay, ctx->max_wire_delay,
@@ -377,7 +366,7 @@ int simulate_impl(gatspi_ctx* ctx, const gatspi_opts* opts) {
   int64_t widest = ctx->I;
   for (int32_t l = 1; l <= ctx->D; ++l)
     widest = std::max<int64_t>(widest, ctx->lvl_gate_begin[l + 1] - ctx->lvl_gate_begin[l]);
-  while ((int64_t)widest * NW > 0x7ffffff0ll && NW > 1) NW = (NW + 1) / 2;
+  while ((int64_t)widest * NW > 0x7fff0000ll && NW > 1) NW = (NW + 1) / 2;
 
   ctx->W = W;
   ctx->n_windows = n_windows;
@@ -401,9 +390,9 @@ int simulate_impl(gatspi_ctx* ctx, const gatspi_opts* opts) {
   auto want_bytes = [&](int32_t nw) {
     const int64_t items = (int64_t)ctx->N * nw;
     int64_t edges = std::max<int64_t>(ctx->times_cap_hint, items * 2 + (1 << 20));
-    return fixed_bytes(ctx, nw, tile) + (size_t)edges * 4;
+    return fixed_bytes(ctx, nw) + (size_t)edges * 4;
   };
-  while (NW > 1 && fixed_bytes(ctx, NW, tile) * 2 > ctx->arena_limit) NW = (NW + 1) / 2;
+  while (NW > 1 && fixed_bytes(ctx, NW) * 2 > ctx->arena_limit) NW = (NW + 1) / 2;
 
   int32_t w0 = 0;
   int64_t edges_total = 0;
@@ -412,7 +401,7 @@ int simulate_impl(gatspi_ctx* ctx, const gatspi_opts* opts) {
     int rc = ensure_arena(ctx, want_bytes(nw));
     if (rc) return rc;
     size_t fixed = 0;
-    if (!plan_batch(ctx, nw, tile, &fixed)) {
+    if (!plan_batch(ctx, nw, &fixed)) {
       if (NW == 1) return fail(ctx, GATSPI_ECAPACITY, "arena too small for one window");
       NW = (NW + 1) / 2;
       continue;
@@ -435,13 +424,14 @@ int simulate_impl(gatspi_ctx* ctx, const gatspi_opts* opts) {
       CK(cudaEventRecord(ev_first, ctx->stream));
       first_recorded = true;
     }
-    CK(cudaMemsetAsync(ctx->d_tile_state, 0, ctx->scratch_bytes, ctx->stream));
+    CK(cudaMemsetAsync(ctx->d_counters, 0, ctx->scratch_bytes, ctx->stream));
     CK(cudaMemsetAsync(ctx->d_status, 0, sizeof(int32_t), ctx->stream));
     {
       InputParams q{};
       q.edge_ptr = ctx->d_edge_ptr; q.edge_time = ctx->d_edge_time; q.init_in = ctx->d_init_in;
-      q.in_prefix = ctx->d_in_prefix; q.init = ctx->d_init; q.off = ctx->d_off; q.times = ctx->d_times;
+      q.in_prefix = ctx->d_in_prefix; q.rstart = ctx->d_rstart; q.rmeta = ctx->d_rmeta; q.times = ctx->d_times;
       q.saif_t1 = ctx->d_t1; q.saif_tc = ctx->d_tc; q.total = l0; q.lvl_base = ctx->d_lvl_base;
+      q.status = ctx->d_status;
       q.I = ctx->I; q.NW = nw; q.w0 = w0; q.W = W; q.C = ctx->C; q.L = ctx->L;
       q.n_items = ctx->I * nw;
       if (o.time_kernels) CK(cudaEventRecord(ctx->ev[0], ctx->stream));
@@ -454,19 +444,19 @@ int simulate_impl(gatspi_ctx* ctx, const gatspi_opts* opts) {
     job.fanin_ptr = ctx->d_fanin_ptr; job.fanin_net = ctx->d_fanin_net; job.lut = ctx->d_lut;
     job.gate_delay = ctx->d_gate_delay; job.wire_delay = ctx->d_wire_delay;
     job.net_level = ctx->d_net_level; job.gate_delta = ctx->d_gate_delta;
-    job.init = ctx->d_init; job.off = ctx->d_off; job.times = ctx->d_times; job.lvl_base = ctx->d_lvl_base;
+    job.rstart = ctx->d_rstart; job.rmeta = ctx->d_rmeta; job.times = ctx->d_times; job.lvl_base = ctx->d_lvl_base;
     job.capacity = ctx->times_cap; job.saif_t1 = ctx->d_t1; job.saif_tc = ctx->d_tc;
     job.status = ctx->d_status;
     job.I = ctx->I; job.NW = nw; job.w0 = w0; job.W = W; job.C = ctx->C; job.L = ctx->L;
     for (int32_t l = 1; l <= ctx->D; ++l) {
       PropParams p{};
       p.job = job;
-      p.seg.tile_state = ctx->d_tile_state + ctx->tile_base[l];
+      p.seg.counters = ctx->d_counters + l;
       p.seg.level = l;
       p.seg.gate_begin = ctx->lvl_gate_begin[l];
-      p.seg.net_end = ctx->I + ctx->lvl_gate_begin[l + 1];
       p.seg.n_items = (ctx->lvl_gate_begin[l + 1] - ctx->lvl_gate_begin[l]) * nw;
-      p.seg.n_tiles = (p.seg.n_items + tile - 1) / tile;
+      p.seg.n_tiles = (int32_t)level_tiles(ctx->lvl_gate_begin[l + 1] - ctx->lvl_gate_begin[l], nw, ipt);
+      p.seg.wide = wide_tiling(nw, ipt) ? 1 : 0;
       p.tile_counter = ctx->d_tile_counter + l;
       if (o.time_kernels) CK(cudaEventRecord(ctx->ev[2 * l], ctx->stream));
       SingleLaunch go{&p, ctx->stream};
@@ -492,6 +482,9 @@ int simulate_impl(gatspi_ctx* ctx, const gatspi_opts* opts) {
         ctx->times_cap_hint = std::max<int64_t>(ctx->times_cap_hint, ctx->times_cap) * 2;
       } else if (NW > 1) {
         NW = (NW + 1) / 2;
+      } else if (status & kStOffset) {
+        return fail(ctx, GATSPI_ECAPACITY,
+                    "a net has more than 32767 edges in one window: use fewer cycles per window");
       } else {
         return fail(ctx, GATSPI_ECAPACITY, "waveforms of one window exceed the arena");
       }
@@ -648,8 +641,8 @@ int gatspi_read_window(gatspi_ctx* ctx, int32_t window, uint8_t* init, int64_t* 
       rc = fail(ctx, GATSPI_ENOMEM, "read-back buffers");
       break;
     }
-    window_counts_kernel<<<(N + 255) / 256, 256, 0, ctx->stream>>>(N, ctx->batch_nw, w, ctx->d_net_level,
-                                                                   ctx->d_off, ctx->d_init, d_cnt, d_iv);
+    window_counts_kernel<<<(N + 255) / 256, 256, 0, ctx->stream>>>(N, ctx->batch_nw, w, ctx->d_rmeta, d_cnt,
+                                                                   d_iv);
     if (cudaMemcpyAsync(cnt.data(), d_cnt, sizeof(int32_t) * N, cudaMemcpyDeviceToHost, ctx->stream) ||
         cudaMemcpyAsync(iv.data(), d_iv, N, cudaMemcpyDeviceToHost, ctx->stream) ||
         cudaStreamSynchronize(ctx->stream)) {
@@ -681,8 +674,8 @@ int gatspi_read_window(gatspi_ctx* ctx, int32_t window, uint8_t* init, int64_t* 
       break;
     }
     window_gather_kernel<<<(N + 255) / 256, 256, 0, ctx->stream>>>(N, ctx->batch_nw, w, ctx->d_net_level,
-                                                                   ctx->d_off, ctx->d_lvl_base, ctx->d_times,
-                                                                   d_dst, d_out);
+                                                                   ctx->d_rstart, ctx->d_rmeta, ctx->d_lvl_base,
+                                                                   ctx->d_times, d_dst, d_out);
     if (cudaMemcpyAsync(times, d_out, sizeof(int32_t) * tot, cudaMemcpyDeviceToHost, ctx->stream) ||
         cudaStreamSynchronize(ctx->stream)) {
       rc = fail(ctx, GATSPI_ECUDA, "read-back copy failed");

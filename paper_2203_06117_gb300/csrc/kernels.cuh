@@ -1,28 +1,29 @@
 // Device code of the re-simulator: input restructuring, the per-level
 // propagation kernel, and waveform read-back.
 //
-// Propagation (GATSPI, Section 3 and Algorithm 1): one thread per (gate,
-// window) item of a logic level.  Each thread merges its fanin pins'
-// delayed, inertially filtered edges, evaluates the truth table, picks the
-// switching pin's (COND) delay, applies the gate inertial filter and emits
-// the output edges.  The paper simulates every item twice (a counting pass,
-// then a storing pass at the scanned offsets); here one pass suffices:
-// edges are staged in shared memory while the block's edge counts are
-// scanned, and the block's global offset comes from a decoupled look-back
-// scan across blocks (Merrill and Garland, "Single-pass Parallel Prefix Scan
-// with Decoupled Look-back", NVIDIA TR 2016).  Fanin waveforms are therefore
-// read from HBM once per pin instead of twice.
+// Propagation (GATSPI, Section 3 and Algorithm 1): each thread takes a few
+// consecutive (gate, window) items of a logic level.  For each it merges
+// the fanin pins' delayed, inertially filtered edges, evaluates the truth
+// table, picks the switching pin's (COND) delay, applies the gate inertial
+// filter and emits the output edges.
+//
+// Output allocation.  The paper simulates every item twice: a counting
+// pass, then a storing pass at the scanned offsets.  Here one pass suffices.
+// A warp stages its items' edges in shared memory, sums its edge count with
+// shuffles, and takes its output range with one atomic add on the level's
+// counter.  Records therefore carry their own start and count, and no tile
+// waits for another.  The same add counts the tile as done (the counter
+// packs tiles done above the edges allocated), so the level's last tile
+// sees the final edge total and publishes it, which places the next level.
 //
 // Waveform store (one batch of NW windows):
-//   init[n*NW + w]            uint8   value of net n at the start of window w
-//   off[n*NW + w + level(n)]  int32   first edge of (n, w), relative to the
-//                                     level's base; every level keeps one
-//                                     extra slot at its end, so the edges of
-//                                     (n, w) end at the next slot
-//   times[lvl_base[level(n)] + off ...]  int32 edge times, window-relative
-// Items of a level are ordered gate-major, window-minor, so the windows of a
-// net are contiguous and a warp's reads of one pin cover one contiguous
-// range.
+//   rstart[n*NW + w]  int32   first edge of (net n, window w), relative to
+//                             lvl_base[level(n)]
+//   rmeta[n*NW + w]   uint16  bit 15: value at the window start; bits 0-14:
+//                             edge count
+//   times[lvl_base[level(n)] + rstart ...]  int32 window-relative edge times
+// The records of a net's windows are contiguous, so a warp's record loads
+// for one pin cover one contiguous range.
 #pragma once
 
 #include <cstdint>
@@ -31,22 +32,19 @@ namespace gatspi_dev {
 namespace {  // every translation unit gets its own copy of the kernels
 
 constexpr int32_t kInf = 0x7fffffff;
-// output edges per thread staged in shared memory (two NT x cap int32
-// buffers per block stay under the 48 KB static limit)
-template <int NT>
-__host__ __device__ constexpr int staging_cap() { return NT >= 512 ? 8 : 16; }
+constexpr int32_t kMaxCount = 0x7fff;  // edges per (net, window) record
+
+// Level counter: tiles done in the top 27 bits, edges allocated in the low
+// 37.  A level has fewer than 2^27 tiles (fewer than 2^31 items, at least 16
+// per tile on average) and fewer than 2^37 edges (512 GB of times).
+constexpr int kTileShift = 37;
+constexpr unsigned long long kEdgeMask = (1ull << kTileShift) - 1ull;
 
 // status bits (device -> host)
 constexpr int kStCapacity = 1;  // arena too small for this batch
-constexpr int kStTimeout = 2;   // look-back wait ran out
+constexpr int kStTimeout = 2;   // reserved: a bounded device-side wait ran out
 constexpr int kStCorrupt = 4;   // a record failed its bounds check
-constexpr int kStOffset = 8;    // a level's edges exceed the int32 offset range
-
-// look-back state word: 2 flag bits over a 62-bit value
-constexpr unsigned long long kFlagAggregate = 1ull << 62;
-constexpr unsigned long long kFlagPrefix = 2ull << 62;
-constexpr unsigned long long kValueMask = (1ull << 62) - 1;
-constexpr long long kSpinLimit = 1ll << 20;  // bounded wait (well under a second)
+constexpr int kStOffset = 8;    // a level's edges exceed int32, or a record > kMaxCount
 
 // One simulation job as the kernels see it: a netlist with its delays, one
 // batch of windows of its stimulus, and where its waveforms and SAIF go.
@@ -60,11 +58,11 @@ struct JobView {
   const int32_t* __restrict__ net_level;   // [N]
   const int32_t* __restrict__ gate_delta;  // [G] delay edit per gate, or null
   // waveform store
-  uint8_t* init;
-  int32_t* off;
+  int32_t* rstart;
+  uint16_t* rmeta;
   int32_t* times;
-  long long* lvl_base;
-  long long capacity;  // elements of times
+  long long* lvl_base;  // [D+2]
+  long long capacity;   // elements of times
   // SAIF accumulators (per internal net)
   unsigned long long* saif_t1;
   unsigned long long* saif_tc;
@@ -78,12 +76,14 @@ struct JobView {
 
 // One level of one job inside a launch.
 struct SegView {
-  unsigned long long* tile_state;  // [n_tiles] look-back words, zero before use
+  unsigned long long* counters;  // [1]: packed level counter, zero before use
   int32_t level;
   int32_t gate_begin;  // first internal gate of the level
-  int32_t net_end;     // one past the level's last net
   int32_t n_items;     // gates of the level * NW
   int32_t n_tiles;
+  int32_t wide;        // 1: tiles of one gate x up to 32*IPT windows, fanin
+                       // waveforms staged in shared memory; 0: tiles of
+                       // 32*IPT consecutive items, fanins read from global
 };
 
 struct PropParams {
@@ -102,6 +102,7 @@ struct MultiParams {
   const JobView* jobs;
   const MultiSeg* segs;  // sorted by tile_begin
   int32_t n_segs;
+  int32_t n_tiles;        // tiles of all segments
   int32_t* tile_counter;  // zero before the launch
 };
 
@@ -125,12 +126,15 @@ struct Pin {
 // parity of j and the start value; the pulse (j, j+1) is dropped when it is
 // narrower than the delay of edge j (Algorithm 1, interconnect inertial
 // test), repeatedly, until an edge survives or the list ends.
+// The edge times may sit in shared memory (staged) or in global memory, so
+// they are read with generic loads (a global-only load of a shared address
+// faults).
 __device__ __forceinline__ void pin_advance(Pin& q) {
   int32_t j = q.j, a = kInf;
   while (j < q.n) {
-    const int32_t t = __ldg(q.t + j);
+    const int32_t t = q.t[j];
     const int32_t d = (((q.v0 ^ (uint32_t)j) & 1u) == 0u) ? q.dr : q.df;
-    if (j + 1 < q.n && __ldg(q.t + j + 1) - t < d) {
+    if (j + 1 < q.n && q.t[j + 1] - t < d) {
       j += 2;
       continue;
     }
@@ -143,11 +147,11 @@ __device__ __forceinline__ void pin_advance(Pin& q) {
 }
 
 // Algorithm 1 for one gate and one window (`edit` shifts every gate delay of
-// the gate, clamped at 1 ps; 0 without a delay edit).  The output keeps at most one
-// edge that may still be cancelled (the last kept one, `pend`): a cancel
-// needs the last kept edge to lie after the current time, and once an edge
-// has been cancelled the kept edge before it is already in the past, so no
-// deeper history is needed.  Edges are handed to `sink` as they become
+// the gate, clamped at 1 ps; 0 without a delay edit).  The output keeps at
+// most one edge that may still be cancelled (the last kept one, `pend`): a
+// cancel needs the last kept edge to lie after the current time, and once an
+// edge has been cancelled the kept edge before it is already in the past, so
+// no deeper history is needed.  Edges are handed to `sink` as they become
 // final; T1 (time at 1 inside [0, len)) is integrated on the way.
 template <int K, class Sink>
 __device__ __forceinline__ void run_gate(Pin (&pin)[K], uint32_t lut,
@@ -205,15 +209,16 @@ __device__ __forceinline__ void run_gate(Pin (&pin)[K], uint32_t lut,
   t1 = acc;
 }
 
-// Appends a thread's output edges to its column of the block's staging
-// buffer (element k of the column at [k * NT]); edges past the cap are dropped
-// and the thread re-simulates straight to global memory later.
-template <int NT>
-struct SmemSink {
+// Appends a lane's output edges to its column of its warp's staging buffer
+// (element k of lane l's column at [k * 32 + l]); edges past the cap are
+// dropped and the lane simulates again straight to global memory once its
+// offsets are known.
+template <int CAP>
+struct WarpSink {
   int32_t* col;
-  int32_t pos;  // edges already staged by this thread's earlier items
+  int32_t pos;  // edges already staged by this lane's earlier windows
   __device__ __forceinline__ void put(int k, int32_t t) {
-    if (pos + k < staging_cap<NT>()) col[(pos + k) * NT] = t;
+    if (pos + k < CAP) col[(pos + k) * 32] = t;
   }
 };
 
@@ -225,248 +230,205 @@ struct GlobalSink {
   }
 };
 
-__device__ __forceinline__ unsigned long long ld_acquire(const unsigned long long* p) {
-  unsigned long long v;
-  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-  return v;
-}
-
-__device__ __forceinline__ void st_release(unsigned long long* p, unsigned long long v) {
-  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
-}
-
-// Load fanin pin pp of item (., w).
-__device__ __forceinline__ void load_pin(const JobView& J, int32_t pp, int32_t w, Pin& q) {
-  const int32_t net = __ldg(J.fanin_net + pp);
-  const int32_t lv = __ldg(J.net_level + net);
-  const long long it = (long long)net * J.NW + w + lv;
-  const int32_t s = __ldg(J.off + it);
-  const int32_t e = __ldg(J.off + it + 1);
-  const long long base = __ldg(J.lvl_base + lv);
-  q.t = J.times + base + s;
-  q.n = e - s;
-  if (s < 0 || q.n < 0 || base + e > J.capacity) {
-    q.n = 0;  // never read outside the arena (only after an earlier error)
+// Record of (net, window): start (relative to its level's base), count and
+// start value; the bounds check keeps reads inside the arena even after an
+// earlier error.
+__device__ __forceinline__ void load_record(const JobView& J, long long rec, long long base,
+                                            int32_t& s, int32_t& n, uint32_t& v0) {
+  s = __ldg(J.rstart + rec);
+  const uint32_t m = __ldg(J.rmeta + rec);
+  n = (int32_t)(m & (uint32_t)kMaxCount);
+  v0 = m >> 15;
+  if (s < 0 || base + s + n > J.capacity) {
+    s = 0;
+    n = 0;
     atomicOr(J.status, kStCorrupt);
   }
-  q.j = 0;
-  q.a = kInf;
-  q.dr = __ldg(J.wire_delay + 2 * pp);
-  q.df = __ldg(J.wire_delay + 2 * pp + 1);
-  q.v0 = __ldg(J.init + (long long)net * J.NW + w);
 }
 
-template <int K, class Sink>
-__device__ __forceinline__ void simulate_k(const JobView& J, int32_t g, int32_t w, int32_t p0,
-                                           Sink& sink, int32_t& count, int32_t& t1,
-                                           uint32_t& y0) {
+// Everything about a gate that does not depend on the window: fetched once
+// and reused for all of a lane's consecutive windows of that gate.
+template <int K>
+struct GateCtx {
+  const int32_t* gd;  // gate delay table of pin 1 (pins follow, 32 entries each)
+  uint32_t lut;
+  int32_t edit;
+  long long rec[K];   // record index of (driving net, window 0): net * NW
+  long long base[K];  // times index of the driving net's level
+  int32_t dr[K], df[K];
+};
+
+template <int K>
+__device__ __forceinline__ void load_gate(const JobView& J, int32_t g, GateCtx<K>& c) {
+  const int32_t p0 = __ldg(J.fanin_ptr + g);
+#pragma unroll
+  for (int i = 0; i < K; ++i) {
+    const int32_t pp = p0 + i;
+    const int32_t net = __ldg(J.fanin_net + pp);
+    c.rec[i] = (long long)net * J.NW;
+    c.base[i] = __ldg(J.lvl_base + __ldg(J.net_level + net));
+    c.dr[i] = __ldg(J.wire_delay + 2 * pp);
+    c.df[i] = __ldg(J.wire_delay + 2 * pp + 1);
+  }
+  c.lut = __ldg(J.lut + g);
+  c.edit = J.gate_delta ? __ldg(J.gate_delta + g) : 0;
+  c.gd = J.gate_delay + (long long)p0 * 32;
+}
+
+// Windows w .. w+run-1 of gate g for one lane: counts go to cnt[0..run),
+// edges to the lane's staging column, start values to bits m0.. of y0s.
+template <int K, int CAP>
+__device__ __forceinline__ void simulate_run_k(const JobView& J, int32_t g, int32_t w, int32_t run,
+                                               int32_t* cnt, int32_t* col, int32_t& total,
+                                               uint32_t& y0s, int m0, long long& t1_acc) {
+  GateCtx<K> c;
+  load_gate<K>(J, g, c);
+  for (int32_t j = 0; j < run; ++j) {
+    Pin pin[K];
+#pragma unroll
+    for (int i = 0; i < K; ++i) {
+      int32_t s, n;
+      uint32_t v0;
+      load_record(J, c.rec[i] + w + j, c.base[i], s, n, v0);
+      pin[i] = Pin{J.times + c.base[i] + s, n, 0, kInf, c.dr[i], c.df[i], v0};
+    }
+    WarpSink<CAP> sink{col, total};
+    int32_t n = 0, t1 = 0;
+    uint32_t y0 = 0;
+    run_gate<K>(pin, c.lut, c.gd, c.edit, window_len(J.w0 + w + j, J.W, J.C, J.L), sink, n, t1, y0);
+    cnt[j] = n;
+    total += n;
+    y0s |= y0 << (m0 + j);
+    t1_acc += t1;
+  }
+}
+
+template <int CAP>
+__device__ __forceinline__ void simulate_run(const JobView& J, int32_t g, int32_t w, int32_t run,
+                                             int32_t* cnt, int32_t* col, int32_t& total, uint32_t& y0s,
+                                             int m0, long long& t1_acc) {
+  switch (__ldg(J.fanin_ptr + g + 1) - __ldg(J.fanin_ptr + g)) {
+    case 1: simulate_run_k<1, CAP>(J, g, w, run, cnt, col, total, y0s, m0, t1_acc); break;
+    case 2: simulate_run_k<2, CAP>(J, g, w, run, cnt, col, total, y0s, m0, t1_acc); break;
+    case 3: simulate_run_k<3, CAP>(J, g, w, run, cnt, col, total, y0s, m0, t1_acc); break;
+    default: simulate_run_k<4, CAP>(J, g, w, run, cnt, col, total, y0s, m0, t1_acc); break;
+  }
+}
+
+// One window of one gate straight to global memory (lanes whose edges did
+// not fit their staging column).
+template <int K>
+__device__ __forceinline__ int32_t simulate_global_k(const JobView& J, int32_t g, int32_t w, int32_t* dst,
+                                                     long long limit) {
+  GateCtx<K> c;
+  load_gate<K>(J, g, c);
   Pin pin[K];
 #pragma unroll
-  for (int i = 0; i < K; ++i) load_pin(J, p0 + i, w, pin[i]);
-  const uint32_t lut = __ldg(J.lut + g);
-  const int32_t edit = J.gate_delta ? __ldg(J.gate_delta + g) : 0;
-  const int32_t len = window_len(J.w0 + w, J.W, J.C, J.L);
-  run_gate<K>(pin, lut, J.gate_delay + (long long)p0 * 32, edit, len, sink, count, t1, y0);
+  for (int i = 0; i < K; ++i) {
+    int32_t s, n;
+    uint32_t v0;
+    load_record(J, c.rec[i] + w, c.base[i], s, n, v0);
+    pin[i] = Pin{J.times + c.base[i] + s, n, 0, kInf, c.dr[i], c.df[i], v0};
+  }
+  GlobalSink sink{dst, limit};
+  int32_t n = 0, t1 = 0;
+  uint32_t y0 = 0;
+  run_gate<K>(pin, c.lut, c.gd, c.edit, window_len(J.w0 + w, J.W, J.C, J.L), sink, n, t1, y0);
+  return n;
 }
 
-template <class Sink>
-__device__ __forceinline__ void simulate_item(const JobView& J, int32_t g, int32_t w,
-                                              Sink& sink, int32_t& count, int32_t& t1,
-                                              uint32_t& y0) {
-  const int32_t p0 = __ldg(J.fanin_ptr + g);
-  switch (__ldg(J.fanin_ptr + g + 1) - p0) {
-    case 1: simulate_k<1>(J, g, w, p0, sink, count, t1, y0); break;
-    case 2: simulate_k<2>(J, g, w, p0, sink, count, t1, y0); break;
-    case 3: simulate_k<3>(J, g, w, p0, sink, count, t1, y0); break;
-    default: simulate_k<4>(J, g, w, p0, sink, count, t1, y0); break;
+__device__ __forceinline__ int32_t simulate_global(const JobView& J, int32_t g, int32_t w, int32_t* dst,
+                                                   long long limit) {
+  switch (__ldg(J.fanin_ptr + g + 1) - __ldg(J.fanin_ptr + g)) {
+    case 1: return simulate_global_k<1>(J, g, w, dst, limit);
+    case 2: return simulate_global_k<2>(J, g, w, dst, limit);
+    case 3: return simulate_global_k<3>(J, g, w, dst, limit);
+    default: return simulate_global_k<4>(J, g, w, dst, limit);
   }
 }
 
-// One tile of one job's level: NT threads x IPT items, items in
-// gate-major, window-minor order, thread t taking IPT consecutive items
-// (consecutive windows of one gate, so its gate metadata is fetched once
-// and its records and edges are contiguous).  Simulate, scan the edge
-// counts, find the tile's offset by look-back, write records and edges, and
-// add the tile's SAIF.  Called by every thread of the block.
-template <int NT, int IPT>
-__device__ __forceinline__ void propagate_tile(const JobView& J, const SegView& S, int32_t tile) {
-  constexpr int NWARP = NT / 32;
-  constexpr int TILE = NT * IPT;
-  constexpr int kCap = staging_cap<NT>();
-  __shared__ int32_t s_scr[kCap * NT];
-  __shared__ int32_t s_cmp[kCap * NT];
-  __shared__ long long s_wsum[NWARP];
-  __shared__ int32_t s_over;
-  __shared__ long long s_prefix, s_base;
+// Per-warp shared memory.  Both tilings use the output staging (each lane's
+// column, the compacted tile, per-window edge counts); the gate-aligned
+// tiling also stages, per fanin pin, the windows' record starts, counts and
+// start values and the edge times they cover.
+template <int IPT>
+struct WarpSmem {
+  static constexpr int TW = 32 * IPT;    // windows (items) per tile
+  static constexpr int TCAP = 2 * TW;    // edge times staged per pin
+  static constexpr int CAP = 8;          // output edges staged per lane
+  int32_t sstart[4][TW];
+  int32_t stimes[4][TCAP];
+  int32_t scr[CAP * 32];
+  int32_t cmp[CAP * 32];
+  int32_t cnt[TW];
+  uint16_t smeta[4][TW];
+};
 
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  if (tid == 0) {
-    s_over = 0;
-    s_base = J.lvl_base[S.level];
-  }
-  __syncthreads();
-  const int32_t r0 = tile * TILE + tid * IPT;  // this thread's first item
-  const int32_t n_mine = max(0, min(IPT, S.n_items - r0));
-  int32_t cnt[IPT];
-  uint32_t y0s = 0;
-  int32_t total = 0;
-  // SAIF partial sums for the thread's current gate
-  int32_t cur_gl = -1;
-  long long acc_t1 = 0, acc_tc = 0;
-  int32_t gl = 0, w = 0;
-  if (n_mine > 0) {
-    gl = r0 / J.NW;
-    w = r0 - gl * J.NW;
-  }
-#pragma unroll
-  for (int m = 0; m < IPT; ++m) {
-    cnt[m] = 0;
-    if (m < n_mine) {
-      if (gl != cur_gl) {
-        if (cur_gl >= 0) {  // gate changed inside the thread's items (small NW)
-          const long long n = (long long)J.I + S.gate_begin + cur_gl;
-          if (acc_t1) atomicAdd(J.saif_t1 + n, (unsigned long long)acc_t1);
-          if (acc_tc) atomicAdd(J.saif_tc + n, (unsigned long long)acc_tc);
-        }
-        cur_gl = gl;
-        acc_t1 = acc_tc = 0;
-      }
-      SmemSink<NT> sink{s_scr + tid, total};
-      int32_t c = 0, t1 = 0;
-      uint32_t y0 = 0;
-      simulate_item(J, S.gate_begin + gl, w, sink, c, t1, y0);
-      cnt[m] = c;
-      total += c;
-      y0s |= y0 << m;
-      acc_t1 += t1;
-      acc_tc += c;
-      if (++w == J.NW) {
-        w = 0;
-        ++gl;
-      }
-    }
-  }
-  if (total > kCap) s_over = 1;
-
-  // block-wide exclusive scan of the per-thread edge counts
+// Everything after a tile's simulation: sum the lanes' edge counts with
+// shuffles, take the tile's output range with one atomic add (which also
+// counts the tile done), write the records (start, count and start value of
+// each item), store the edges (compacted through shared memory, or, when a
+// lane's staging column overflowed, by `resim` straight to their final
+// place), and add the SAIF of the lane's last gate.  The level's last tile
+// to take its range publishes the level's edge total as the next level's
+// base; later kernels see it after this launch ends.
+template <int IPT, class Resim>
+__device__ __forceinline__ void finish_tile(const JobView& J, const SegView& S, int lane, WarpSmem<IPT>& sm,
+                                            int32_t n_mine, const int32_t* cnt, int32_t total, uint32_t y0s,
+                                            long long rec_first, int32_t cur_gl, long long acc_t1,
+                                            long long acc_tc, Resim&& resim) {
+  constexpr int CAP = WarpSmem<IPT>::CAP;
+  const bool any_over = __any_sync(0xffffffffu, total > CAP);
   int32_t incl = total;
 #pragma unroll
   for (int d = 1; d < 32; d <<= 1) {
     const int32_t v = __shfl_up_sync(0xffffffffu, incl, d);
     if (lane >= d) incl += v;
   }
-  if (lane == 31) s_wsum[warp] = incl;
-  __syncthreads();
-  if (warp == 0) {
-    long long v = lane < NWARP ? s_wsum[lane] : 0;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-      const long long u = __shfl_up_sync(0xffffffffu, v, d);
-      if (lane >= d) v += u;
-    }
-    if (lane < NWARP) s_wsum[lane] = v;
-  }
-  __syncthreads();
-  const long long excl_local = (warp ? s_wsum[warp - 1] : 0) + incl - total;
-  const long long aggregate = s_wsum[NWARP - 1];
-
-  // decoupled look-back: this block's offset among all blocks of the level
-  if (warp == 0) {
-    long long excl = 0;
-    if (tile == 0) {
-      if (lane == 0) st_release(S.tile_state, kFlagPrefix | (unsigned long long)aggregate);
-    } else {
-      if (lane == 0) st_release(S.tile_state + tile, kFlagAggregate | (unsigned long long)aggregate);
-      int32_t pos = tile - 1;
-      long long spins = 0;
-      for (;;) {
-        const int32_t idx = pos - lane;
-        const unsigned long long word = idx >= 0 ? ld_acquire(S.tile_state + idx) : kFlagPrefix;
-        const unsigned long long flag = word & ~kValueMask;
-        if (__any_sync(0xffffffffu, flag == 0)) {
-          if (++spins > kSpinLimit) {
-            if (lane == 0) atomicOr(J.status, kStTimeout);
-            break;
-          }
-          __nanosleep(64);
-          continue;
-        }
-        const unsigned pmask = __ballot_sync(0xffffffffu, flag == kFlagPrefix);
-        long long val = (long long)(word & kValueMask);
-        if (pmask) {
-          const int first = __ffs(pmask) - 1;
-          if (lane > first) val = 0;
-        }
-#pragma unroll
-        for (int d = 16; d > 0; d >>= 1) val += __shfl_xor_sync(0xffffffffu, val, d);
-        excl += val;
-        if (pmask) break;
-        pos -= 32;
-      }
-      if (lane == 0) st_release(S.tile_state + tile, kFlagPrefix | (unsigned long long)(excl + aggregate));
-    }
-    if (lane == 0) s_prefix = excl;
-  }
-  __syncthreads();
-  const long long prefix = s_prefix;
-  const long long base = s_base;
-  const long long my_off = prefix + excl_local;
-
-  // records: offset and start value of every item; a level's record index
-  // is linear in the item index
-  {
-    const long long rec = ((long long)J.I + S.gate_begin) * J.NW + r0;
-    long long o = my_off;
-#pragma unroll
-    for (int m = 0; m < IPT; ++m) {
-      if (m < n_mine) {
-        J.off[rec + S.level + m] = (int32_t)o;
-        J.init[rec + m] = (uint8_t)((y0s >> m) & 1u);
-        o += cnt[m];
-      }
-    }
-    if (n_mine > 0 && o > 0x7fffffffll) atomicOr(J.status, kStOffset);
-  }
-  if (tile == S.n_tiles - 1 && tid == 0) {
-    const long long tot = prefix + aggregate;
+  const long long excl_l = incl - total;
+  const long long aggregate = __shfl_sync(0xffffffffu, incl, 31);
+  unsigned long long old = 0;
+  if (lane == 0) old = atomicAdd(S.counters, (1ull << kTileShift) + (unsigned long long)aggregate);
+  old = __shfl_sync(0xffffffffu, old, 0);
+  const long long start = (long long)(old & kEdgeMask);
+  const long long base = __ldg(J.lvl_base + S.level);
+  if (lane == 0 && (long long)(old >> kTileShift) == (long long)S.n_tiles - 1) {
+    const long long tot = start + aggregate;
     if (tot > 0x7fffffffll) atomicOr(J.status, kStOffset);
-    J.off[(long long)S.net_end * J.NW + S.level] = (int32_t)tot;
     J.lvl_base[S.level + 1] = base + tot;
     if (base + tot > J.capacity) atomicOr(J.status, kStCapacity);
   }
 
-  // edges
-  int32_t* dst = J.times + base + prefix;
-  const long long room = J.capacity - base - prefix;  // elements left in the arena
-  if (!s_over) {
-    for (int k = 0; k < total; ++k) s_cmp[excl_local + k] = s_scr[k * NT + tid];
-    __syncthreads();
-    const long long n = aggregate < room ? aggregate : (room > 0 ? room : 0);
-    for (long long j = tid; j < n; j += NT) dst[j] = s_cmp[j];
-  } else if (n_mine > 0) {
-    if (total <= kCap) {
-      for (int k = 0; k < total; ++k)
-        if (excl_local + k < room) dst[excl_local + k] = s_scr[k * NT + tid];
-    } else {
-      // more edges than the staging column holds: simulate again, straight
-      // to the final positions
-      int32_t g2 = r0 / J.NW, w2 = r0 - g2 * J.NW;
-      long long o = excl_local;
-      for (int m = 0; m < n_mine; ++m) {
-        GlobalSink gs{dst + o, room - o};
-        int32_t c2, t2;
-        uint32_t y2;
-        simulate_item(J, S.gate_begin + g2, w2, gs, c2, t2, y2);
-        o += c2;
-        if (++w2 == J.NW) {
-          w2 = 0;
-          ++g2;
-        }
-      }
+  {
+    long long o = start + excl_l;
+    for (int m = 0; m < n_mine; ++m) {
+      const int32_t c = cnt[m];
+      J.rstart[rec_first + m] = (int32_t)o;
+      J.rmeta[rec_first + m] = (uint16_t)(min(c, kMaxCount) | (int32_t)(((y0s >> m) & 1u) << 15));
+      if (c > kMaxCount) atomicOr(J.status, kStOffset);
+      o += c;
     }
+    if (n_mine > 0 && o > 0x7fffffffll) atomicOr(J.status, kStOffset);
   }
 
-  // SAIF: the thread's last gate; one atomic per warp when the warp agrees
+  int32_t* dst = J.times + base + start;
+  const long long room = J.capacity - base - start;  // elements left in the arena
+  if (!any_over) {
+    for (int k = 0; k < total; ++k) sm.cmp[excl_l + k] = sm.scr[k * 32 + lane];
+    __syncwarp();
+    const long long n = aggregate < room ? aggregate : (room > 0 ? room : 0);
+    for (long long j = lane; j < n; j += 32) dst[j] = sm.cmp[j];
+  } else if (n_mine > 0) {
+    if (total <= CAP) {
+      for (int k = 0; k < total; ++k)
+        if (excl_l + k < room) dst[excl_l + k] = sm.scr[k * 32 + lane];
+    } else {
+      resim(dst, excl_l, room);
+    }
+  }
+  __syncwarp();
+
+  // SAIF: the lane's last gate; one atomic per warp when the warp agrees
   // (every lane takes part in every shuffle)
   const int32_t g_lane0 = __shfl_sync(0xffffffffu, cur_gl, 0);
   const bool uniform = __all_sync(0xffffffffu, cur_gl < 0 || cur_gl == g_lane0);
@@ -489,36 +451,258 @@ __device__ __forceinline__ void propagate_tile(const JobView& J, const SegView& 
   }
 }
 
-template <int NT, int IPT>
-__global__ void __launch_bounds__(NT) propagate_kernel(const __grid_constant__ PropParams p) {
-  __shared__ int32_t s_tile;
-  if (threadIdx.x == 0) s_tile = atomicAdd(p.tile_counter, 1);
-  __syncthreads();
-  propagate_tile<NT, IPT>(p.job, p.seg, s_tile);
+// Linear tiling: 32 lanes x IPT consecutive items of the level in
+// gate-major order (a tile may span gates); each lane fetches its gate's
+// metadata once and reads its fanin records and edges from global memory.
+template <int IPT>
+__device__ __forceinline__ void linear_tile(const JobView& J, const SegView& S, int32_t tile, WarpSmem<IPT>& sm) {
+  constexpr int CAP = WarpSmem<IPT>::CAP;
+  const int lane = threadIdx.x & 31;
+  const int32_t r0 = tile * (32 * IPT) + lane * IPT;  // this lane's first item
+  const int32_t n_mine = max(0, min(IPT, S.n_items - r0));
+  int32_t* cnt = sm.cnt + lane * IPT;
+  int32_t total = 0;
+  uint32_t y0s = 0;
+  int32_t cur_gl = -1;  // SAIF partial sums for the lane's current gate
+  long long acc_t1 = 0, acc_tc = 0;
+  if (n_mine > 0) {
+    int32_t gl = r0 / J.NW, w = r0 - gl * J.NW, m = 0;
+    while (m < n_mine) {
+      const int32_t run = min(n_mine - m, J.NW - w);
+      if (cur_gl >= 0) {  // the lane's windows cross into the next gate (small NW)
+        const long long n = (long long)J.I + S.gate_begin + cur_gl;
+        if (acc_t1) atomicAdd(J.saif_t1 + n, (unsigned long long)acc_t1);
+        if (acc_tc) atomicAdd(J.saif_tc + n, (unsigned long long)acc_tc);
+      }
+      cur_gl = gl;
+      acc_t1 = 0;
+      const int32_t before = total;
+      simulate_run<CAP>(J, S.gate_begin + gl, w, run, cnt + m, sm.scr + lane, total, y0s, m, acc_t1);
+      acc_tc = total - before;
+      m += run;
+      ++gl;
+      w = 0;
+    }
+  }
+  // a level's records are linear in its item index
+  const long long rec_first = ((long long)J.I + S.gate_begin) * J.NW + r0;
+  finish_tile<IPT>(J, S, lane, sm, n_mine, cnt, total, y0s, rec_first, cur_gl, acc_t1, acc_tc,
+                   [&](int32_t* dst, long long o, long long room) {
+                     int32_t gl = r0 / J.NW, w = r0 - gl * J.NW;
+                     for (int m = 0; m < n_mine; ++m) {
+                       o += simulate_global(J, S.gate_begin + gl, w, dst + o, room - o);
+                       if (++w == J.NW) {
+                         w = 0;
+                         ++gl;
+                       }
+                     }
+                   });
 }
 
-// Several jobs (each at its own level) in one launch: tiles are taken in
-// launch order and mapped to (job, level) segments, each segment with its
-// own look-back chain.
+// Gate-aligned tiling, K pins: one gate x n <= 32*IPT consecutive windows.
+// The warp first stages, for every pin, the n records and the edge times
+// they cover into shared memory with coalesced loads all in flight
+// together, then each lane simulates its IPT windows reading shared memory
+// only (a pin whose edges exceed the staging room, or are not one
+// contiguous range, is read from global memory instead).
+template <int K, int IPT>
+__device__ __forceinline__ void wide_tile_k(const JobView& J, const SegView& S, int32_t gl, int32_t wb,
+                                            int32_t n, WarpSmem<IPT>& sm) {
+  constexpr int CAP = WarpSmem<IPT>::CAP;
+  constexpr int TCAP = WarpSmem<IPT>::TCAP;
+  const int lane = threadIdx.x & 31;
+  const int32_t g = S.gate_begin + gl;
+  const int32_t p0 = __ldg(J.fanin_ptr + g);
+  long long base[K];
+  int32_t s0[K], dr[K], df[K];
+  bool staged[K];
+#pragma unroll
+  for (int i = 0; i < K; ++i) {
+    const int32_t pp = p0 + i;
+    const int32_t net = __ldg(J.fanin_net + pp);
+    const long long rec = (long long)net * J.NW + wb;
+    base[i] = __ldg(J.lvl_base + __ldg(J.net_level + net));
+    dr[i] = __ldg(J.wire_delay + 2 * pp);
+    df[i] = __ldg(J.wire_delay + 2 * pp + 1);
+    for (int j = lane; j < n; j += 32) {
+      sm.sstart[i][j] = __ldg(J.rstart + rec + j);
+      sm.smeta[i][j] = __ldg(J.rmeta + rec + j);
+    }
+  }
+  __syncwarp();
+  // a pin's edges for these windows are one range when each record starts
+  // where the previous one ends (records of one producing tile); stage the
+  // range then, else read the pin from global memory
+#pragma unroll
+  for (int i = 0; i < K; ++i) {
+    bool ok = true;
+    int32_t lo = kInf, hi = 0;
+    for (int j = lane; j < n; j += 32) {
+      const int32_t s = sm.sstart[i][j], c = sm.smeta[i][j] & kMaxCount;
+      if (s < 0 || base[i] + s + c > J.capacity) ok = false;
+      lo = min(lo, s);
+      hi = max(hi, s + c);
+      if (j + 1 < n && sm.sstart[i][j + 1] != s + c) ok = false;
+    }
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+      lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, d));
+      hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, d));
+    }
+    ok = __all_sync(0xffffffffu, ok);
+    s0[i] = lo == kInf ? 0 : lo;
+    const int32_t m = hi - s0[i];
+    staged[i] = ok && m >= 0 && m <= TCAP;
+    if (staged[i]) {
+      const int32_t* src = J.times + base[i] + s0[i];
+      for (int j = lane; j < m; j += 32) sm.stimes[i][j] = __ldg(src + j);
+    }
+  }
+  __syncwarp();
+  const uint32_t lut = __ldg(J.lut + g);
+  const int32_t edit = J.gate_delta ? __ldg(J.gate_delta + g) : 0;
+  const int32_t* gd = J.gate_delay + (long long)p0 * 32;
+  const int32_t w_first = lane * IPT;  // this lane's first window inside the tile
+  const int32_t n_mine = max(0, min(IPT, n - w_first));
+  int32_t* cnt = sm.cnt + w_first;
+  int32_t total = 0;
+  uint32_t y0s = 0;
+  long long acc_t1 = 0;
+  auto pins_of = [&](int32_t wl, Pin (&pin)[K]) {
+#pragma unroll
+    for (int i = 0; i < K; ++i) {
+      int32_t s = sm.sstart[i][wl];
+      const uint32_t meta = sm.smeta[i][wl];
+      int32_t c = (int32_t)(meta & (uint32_t)kMaxCount);
+      if (s < 0 || base[i] + s + c > J.capacity) {  // never read outside the arena
+        atomicOr(J.status, kStCorrupt);
+        s = 0;
+        c = 0;
+      }
+      pin[i].t = staged[i] ? &sm.stimes[i][s - s0[i]] : J.times + base[i] + s;
+      pin[i].n = c;
+      pin[i].j = 0;
+      pin[i].a = kInf;
+      pin[i].dr = dr[i];
+      pin[i].df = df[i];
+      pin[i].v0 = meta >> 15;
+    }
+  };
+  for (int m = 0; m < n_mine; ++m) {
+    const int32_t wl = w_first + m;
+    Pin pin[K];
+    pins_of(wl, pin);
+    WarpSink<CAP> sink{sm.scr + lane, total};
+    int32_t c = 0, t1 = 0;
+    uint32_t y0 = 0;
+    run_gate<K>(pin, lut, gd, edit, window_len(J.w0 + wb + wl, J.W, J.C, J.L), sink, c, t1, y0);
+    cnt[m] = c;
+    total += c;
+    y0s |= y0 << m;
+    acc_t1 += t1;
+  }
+  const long long rec_first = ((long long)J.I + g) * J.NW + wb + w_first;
+  finish_tile<IPT>(J, S, lane, sm, n_mine, cnt, total, y0s, rec_first, n_mine > 0 ? gl : -1, acc_t1, total,
+                   [&](int32_t* dst, long long o, long long room) {
+                     for (int m = 0; m < n_mine; ++m) {
+                       const int32_t wl = w_first + m;
+                       Pin pin[K];
+                       pins_of(wl, pin);
+                       GlobalSink sink{dst + o, room - o};
+                       int32_t c = 0, t1 = 0;
+                       uint32_t y0 = 0;
+                       run_gate<K>(pin, lut, gd, edit, window_len(J.w0 + wb + wl, J.W, J.C, J.L), sink, c,
+                                   t1, y0);
+                       o += c;
+                     }
+                   });
+}
+
+template <int IPT>
+__device__ __forceinline__ void wide_tile(const JobView& J, const SegView& S, int32_t tile, WarpSmem<IPT>& sm) {
+  constexpr int TW = 32 * IPT;
+  const int32_t tpg = (J.NW + TW - 1) / TW;  // tiles per gate
+  const int32_t gl = tile / tpg;
+  const int32_t wb = (tile - gl * tpg) * TW;
+  const int32_t n = min(TW, J.NW - wb);
+  const int32_t g = S.gate_begin + gl;
+  switch (__ldg(J.fanin_ptr + g + 1) - __ldg(J.fanin_ptr + g)) {
+    case 1: wide_tile_k<1, IPT>(J, S, gl, wb, n, sm); break;
+    case 2: wide_tile_k<2, IPT>(J, S, gl, wb, n, sm); break;
+    case 3: wide_tile_k<3, IPT>(J, S, gl, wb, n, sm); break;
+    default: wide_tile_k<4, IPT>(J, S, gl, wb, n, sm); break;
+  }
+}
+
+template <int IPT>
+__device__ __forceinline__ void propagate_warp(const JobView& J, const SegView& S, int32_t tile, WarpSmem<IPT>& sm) {
+  if (S.wide) wide_tile<IPT>(J, S, tile, sm);
+  else linear_tile<IPT>(J, S, tile, sm);
+}
+
+// at most 64 registers per thread: 1024 resident threads per SM
+template <int NT>
+__host__ __device__ constexpr int min_blocks() { return 1024 / NT; }
+
+// One level of one job; each warp takes one tile (one atomic per block hands
+// out NT/32 consecutive tiles).
 template <int NT, int IPT>
-__global__ void __launch_bounds__(NT) propagate_multi_kernel(const __grid_constant__ MultiParams m) {
-  __shared__ JobView s_job;
-  __shared__ SegView s_seg;
-  __shared__ int32_t s_tile;
-  if (threadIdx.x == 0) {
-    const int32_t t = atomicAdd(m.tile_counter, 1);
+__global__ void __launch_bounds__(NT, min_blocks<NT>()) propagate_kernel(const __grid_constant__ PropParams p) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  WarpSmem<IPT>* sm = reinterpret_cast<WarpSmem<IPT>*>(smem_raw);
+  __shared__ int32_t s_first;
+  if (threadIdx.x == 0) s_first = atomicAdd(p.tile_counter, NT / 32);
+  __syncthreads();
+  const int32_t t = s_first + (int32_t)(threadIdx.x >> 5);
+  if (t >= p.seg.n_tiles) return;
+  propagate_warp<IPT>(p.job, p.seg, t, sm[threadIdx.x >> 5]);
+}
+
+// Several jobs (each at its own level) in one launch: tiles are handed out
+// as above and mapped to (job, level) segments, each segment with its own
+// counters and tiling.
+template <int NT, int IPT>
+__global__ void __launch_bounds__(NT, min_blocks<NT>()) propagate_multi_kernel(const __grid_constant__ MultiParams m) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  WarpSmem<IPT>* sm = reinterpret_cast<WarpSmem<IPT>*>(smem_raw);
+  __shared__ JobView s_job[NT / 32];
+  __shared__ SegView s_seg[NT / 32];
+  __shared__ int32_t s_first;
+  const int warp = threadIdx.x >> 5;
+  if (threadIdx.x == 0) s_first = atomicAdd(m.tile_counter, NT / 32);
+  __syncthreads();
+  int32_t t = s_first + warp;
+  if (t >= m.n_tiles) return;
+  if ((threadIdx.x & 31) == 0) {
     int32_t lo = 0, hi = m.n_segs - 1;
     while (lo < hi) {  // last segment with tile_begin <= t
       const int32_t mid = (lo + hi + 1) >> 1;
       if (m.segs[mid].tile_begin <= t) lo = mid; else hi = mid - 1;
     }
-    s_seg = m.segs[lo].seg;
-    s_job = m.jobs[m.segs[lo].job];
-    s_tile = t - m.segs[lo].tile_begin;
+    s_seg[warp] = m.segs[lo].seg;
+    s_job[warp] = m.jobs[m.segs[lo].job];
+    t -= m.segs[lo].tile_begin;
   }
-  __syncthreads();
-  propagate_tile<NT, IPT>(s_job, s_seg, s_tile);
+  t = __shfl_sync(0xffffffffu, t, 0);
+  __syncwarp();
+  propagate_warp<IPT>(s_job[warp], s_seg[warp], t, sm[warp]);
 }
+
+// Items per tile (one warp's tile) for a variant.
+inline int tile_items_of(int ipt) { return 32 * ipt; }
+
+// Windows per batch from which a level uses gate-aligned tiles with staged
+// fanins (below, tiles would be mostly empty).
+inline bool wide_tiling(int32_t nw, int ipt) { return nw >= 16 * ipt; }
+
+// Tiles of one level of `gates` gates and nw windows.
+inline long long level_tiles(long long gates, int32_t nw, int ipt) {
+  const long long tw = tile_items_of(ipt);
+  return wide_tiling(nw, ipt) ? gates * ((nw + tw - 1) / tw) : (gates * nw + tw - 1) / tw;
+}
+
+template <int NT, int IPT>
+inline size_t dyn_smem() { return sizeof(WarpSmem<IPT>) * (NT / 32); }
 
 // Host-side launchers of the two propagation kernels for one compiled
 // (threads, items per thread) variant.
@@ -526,15 +710,32 @@ struct SingleLaunch {
   const PropParams* p;
   cudaStream_t s;
   template <int NT, int IPT>
-  void go() { propagate_kernel<NT, IPT><<<p->seg.n_tiles, NT, 0, s>>>(*p); }
+  void go() {
+    static bool attr = false;  // opt in to more than 48 KB of dynamic shared memory once
+    if (!attr) {
+      cudaFuncSetAttribute(propagate_kernel<NT, IPT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)dyn_smem<NT, IPT>());
+      attr = true;
+    }
+    const unsigned grid = (unsigned)((p->seg.n_tiles + NT / 32 - 1) / (NT / 32));
+    propagate_kernel<NT, IPT><<<grid, NT, dyn_smem<NT, IPT>(), s>>>(*p);
+  }
 };
 
 struct MultiLaunch {
   const MultiParams* m;
-  unsigned grid;
   cudaStream_t s;
   template <int NT, int IPT>
-  void go() { propagate_multi_kernel<NT, IPT><<<grid, NT, 0, s>>>(*m); }
+  void go() {
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(propagate_multi_kernel<NT, IPT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)dyn_smem<NT, IPT>());
+      attr = true;
+    }
+    const unsigned grid = (unsigned)((m->n_tiles + NT / 32 - 1) / (NT / 32));
+    propagate_multi_kernel<NT, IPT><<<grid, NT, dyn_smem<NT, IPT>(), s>>>(*m);
+  }
 };
 
 // Launch one of the compiled (threads, items per thread) variants.
@@ -559,19 +760,21 @@ inline bool launch_variant(int nt, int ipt, Launch&& launch) {
 // Level 0: the inputs' records for the batch, read straight from the
 // stimulus (edges of window w = edges of its cycles, shifted onto the
 // window's time axis; start value = initial value toggled by every earlier
-// edge).
+// edge).  Inputs' edges are laid out input-major, so record (i, w) starts at
+// in_prefix[i] + (edges of input i in the batch before window w).
 struct InputParams {
   const int64_t* __restrict__ edge_ptr;   // [I*C+1]
   const int32_t* __restrict__ edge_time;
   const uint8_t* __restrict__ init_in;    // [I]
   const long long* __restrict__ in_prefix;  // [I] edges of inputs < i in this batch
-  uint8_t* init;
-  int32_t* off;
+  int32_t* rstart;
+  uint16_t* rmeta;
   int32_t* times;
   unsigned long long* saif_t1;
   unsigned long long* saif_tc;
   long long total;  // level-0 edges of the batch
   long long* lvl_base;
+  int32_t* status;
   int32_t I, NW, w0, W, C, L;
   int32_t n_items;
 };
@@ -592,8 +795,10 @@ __global__ void inputs_kernel(const InputParams q) {
     const long long b = ep[c1];
     const long long o = q.in_prefix[i] + (a - ep[q.w0 * q.W]);
     uint32_t v = (q.init_in[i] ^ (uint32_t)((a - ep[0]) & 1)) & 1u;
-    q.init[(long long)i * q.NW + w] = (uint8_t)v;
-    q.off[(long long)i * q.NW + w] = (int32_t)o;
+    cnt = (int32_t)(b - a);
+    q.rstart[(long long)i * q.NW + w] = (int32_t)o;
+    q.rmeta[(long long)i * q.NW + w] = (uint16_t)(min(cnt, kMaxCount) | (int32_t)(v << 15));
+    if (cnt > kMaxCount) atomicOr(q.status, kStOffset);
     const int32_t len = (c1 - c0) * q.L;
     int32_t prev = 0;
     long long k = o;
@@ -609,13 +814,12 @@ __global__ void inputs_kernel(const InputParams q) {
       }
     }
     if (v) t1 += len - prev;
-    cnt = (int32_t)(b - a);
   }
   if (r == 0) {
-    q.off[(long long)q.I * q.NW] = (int32_t)q.total;  // level-0 end slot
     q.lvl_base[0] = 0;
     q.lvl_base[1] = q.total;
   }
+  // every lane takes part in every shuffle
   const int32_t i0 = __shfl_sync(0xffffffffu, i, 0);
   const int lane0_valid = __shfl_sync(0xffffffffu, valid ? 1 : 0, 0);
   const bool uniform = __all_sync(0xffffffffu, !valid || i == i0);
@@ -638,28 +842,26 @@ __global__ void inputs_kernel(const InputParams q) {
 
 // Read-back of one window: counts and start values per internal net, then
 // the edges gathered to caller-ordered offsets.
-__global__ void window_counts_kernel(int32_t N, int32_t NW, int32_t w, const int32_t* net_level,
-                                     const int32_t* off, const uint8_t* init, int32_t* cnt,
+__global__ void window_counts_kernel(int32_t N, int32_t NW, int32_t w, const uint16_t* rmeta, int32_t* cnt,
                                      uint8_t* init_out) {
   const int32_t n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= N) return;
-  const long long it = (long long)n * NW + w + net_level[n];
-  cnt[n] = off[it + 1] - off[it];
-  init_out[n] = init[(long long)n * NW + w];
+  const uint32_t m = rmeta[(long long)n * NW + w];
+  cnt[n] = (int32_t)(m & (uint32_t)kMaxCount);
+  init_out[n] = (uint8_t)(m >> 15);
 }
 
 __global__ void window_gather_kernel(int32_t N, int32_t NW, int32_t w, const int32_t* net_level,
-                                     const int32_t* off, const long long* lvl_base,
-                                     const int32_t* times, const long long* dst_ptr,
-                                     int32_t* out) {
+                                     const int32_t* rstart, const uint16_t* rmeta, const long long* lvl_base,
+                                     const int32_t* times, const long long* dst_ptr, int32_t* out) {
   const int32_t n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= N) return;
-  const int32_t lv = net_level[n];
-  const long long it = (long long)n * NW + w + lv;
-  const int32_t s = off[it], e = off[it + 1];
-  const int32_t* src = times + lvl_base[lv] + s;
-  long long d = dst_ptr[n];
-  for (int32_t k = 0; k < e - s; ++k) out[d + k] = src[k];
+  const long long rec = (long long)n * NW + w;
+  const int32_t s = rstart[rec];
+  const int32_t c = (int32_t)(rmeta[rec] & (uint32_t)kMaxCount);
+  const int32_t* src = times + lvl_base[net_level[n]] + s;
+  const long long d = dst_ptr[n];
+  for (int32_t k = 0; k < c; ++k) out[d + k] = src[k];
 }
 
 // Add a finished part's SAIF into its job's accumulators.

@@ -7,8 +7,9 @@
 // reserved all memory up front and must not fail for lack of it mid-run.
 // They allocate the netlist, delay and waveform buffers themselves and pass
 // them in.  The only memory the propagation kernel needs beyond those
-// buffers -- one look-back word per tile of the level and a tile counter --
-// lives in a fixed array in this file, so this entry point never allocates.
+// buffers -- the level's counter (edges allocated, tiles done) and the
+// launch's tile counter -- lives in a fixed array in this file, so this entry point never
+// allocates.
 #include <cuda_runtime.h>
 
 #include <atomic>
@@ -23,16 +24,15 @@ namespace {
 
 constexpr int kNoAllocThreads = 256;
 constexpr int kNoAllocItemsPerThread = 4;
-constexpr int kNoAllocTileItems = kNoAllocThreads * kNoAllocItemsPerThread;
 constexpr int kMaxDevices = 64;
+constexpr int kScratchWords = 32;
 
 }  // namespace
 
-// One look-back word per tile (at most GATSPI_NOALLOC_MAX_TILES tiles in a
-// level), then the launch's tile counter.  Shared by every call on a
-// device; each call clears the part it uses before its kernel runs.
-static __device__ __align__(256) unsigned long long
-    g_noalloc_scratch[GATSPI_NOALLOC_MAX_TILES + 32];
+// Word 0: the level's counter (edges allocated, tiles done); word 1: the
+// launch's tile counter; the rest is unused.  Shared by every call on a
+// device; each call clears it before its kernel runs.
+static __device__ __align__(256) unsigned long long g_noalloc_scratch[kScratchWords];
 
 namespace {
 
@@ -76,47 +76,47 @@ extern "C" int gatspi_propagate_level_noalloc(const gatspi_level_args* a, void* 
   if (!a) return GATSPI_EINVAL;
   if (a->err && a->err_len > 0) a->err[0] = 0;
   if (!a->fanin_ptr || !a->fanin_net || !a->lut || !a->gate_delay || !a->wire_delay || !a->net_level ||
-      !a->init || !a->off || !a->times || !a->lvl_base || !a->saif_t1 || !a->saif_tc || !a->status)
+      !a->rstart || !a->rmeta || !a->times || !a->lvl_base || !a->saif_t1 || !a->saif_tc || !a->status)
     return say(a, GATSPI_EINVAL, "a device pointer is null");
   if (a->num_inputs < 1 || a->level < 1 || a->gate_begin < 0 || a->gate_end <= a->gate_begin ||
       a->num_windows < 1 || a->first_window < 0 || a->window_cycles < 1 || a->num_cycles < 1 ||
       a->cycle_ps < 1 || a->capacity < 0)
     return say(a, GATSPI_EINVAL, "bad level, gate range, window or cycle argument");
   const long long items = (long long)(a->gate_end - a->gate_begin) * a->num_windows;
-  const long long tiles = (items + kNoAllocTileItems - 1) / kNoAllocTileItems;
-  if (items > 0x7fffffffll || tiles > GATSPI_NOALLOC_MAX_TILES)
+  if (items > GATSPI_NOALLOC_MAX_ITEMS)
     return say(a, GATSPI_ECAPACITY,
-               "level too large for the fixed look-back scratch: more than "
-               "GATSPI_NOALLOC_MAX_TILES * 1024 (gate, window) items; use fewer windows per call");
+               "level too large: more than GATSPI_NOALLOC_MAX_ITEMS (gate, window) items; "
+               "use fewer windows per call");
+  const long long tiles = level_tiles(a->gate_end - a->gate_begin, a->num_windows, kNoAllocItemsPerThread);
   int device = 0;
   if (cudaGetDevice(&device) != cudaSuccess) return say(a, GATSPI_ECUDA, "cudaGetDevice failed");
   unsigned long long* scratch = nullptr;
   int rc = scratch_address(device, &scratch);
-  if (rc) return say(a, rc, "cudaGetSymbolAddress of the look-back scratch failed");
+  if (rc) return say(a, rc, "cudaGetSymbolAddress of the counter scratch failed");
   cudaStream_t s = (cudaStream_t)stream;
-  // the look-back words of this level and the tile counter must start at 0
-  if (cudaMemsetAsync(scratch, 0, sizeof(unsigned long long) * (size_t)tiles, s) != cudaSuccess ||
-      cudaMemsetAsync(scratch + GATSPI_NOALLOC_MAX_TILES, 0, sizeof(unsigned long long), s) != cudaSuccess)
-    return say(a, GATSPI_ECUDA, "clearing the look-back scratch failed");
+  // the level's counters and the tile counter must start at 0
+  if (cudaMemsetAsync(scratch, 0, sizeof(unsigned long long) * kScratchWords, s) != cudaSuccess)
+    return say(a, GATSPI_ECUDA, "clearing the counter scratch failed");
   PropParams p{};
   JobView& j = p.job;
   j.fanin_ptr = a->fanin_ptr; j.fanin_net = a->fanin_net; j.lut = a->lut;
   j.gate_delay = a->gate_delay; j.wire_delay = a->wire_delay; j.net_level = a->net_level;
   j.gate_delta = nullptr;
-  j.init = a->init; j.off = a->off; j.times = a->times; j.lvl_base = (long long*)a->lvl_base;
+  j.rstart = a->rstart; j.rmeta = a->rmeta; j.times = a->times; j.lvl_base = (long long*)a->lvl_base;
   j.capacity = a->capacity;
   j.saif_t1 = (unsigned long long*)a->saif_t1; j.saif_tc = (unsigned long long*)a->saif_tc;
   j.status = a->status;
   j.I = a->num_inputs; j.NW = a->num_windows; j.w0 = a->first_window; j.W = a->window_cycles;
   j.C = a->num_cycles; j.L = a->cycle_ps;
-  p.seg.tile_state = scratch;
+  p.seg.counters = scratch;
   p.seg.level = a->level;
   p.seg.gate_begin = a->gate_begin;
-  p.seg.net_end = a->num_inputs + a->gate_end;
   p.seg.n_items = (int32_t)items;
   p.seg.n_tiles = (int32_t)tiles;
-  p.tile_counter = (int32_t*)(scratch + GATSPI_NOALLOC_MAX_TILES);
-  propagate_kernel<kNoAllocThreads, kNoAllocItemsPerThread><<<(unsigned)tiles, kNoAllocThreads, 0, s>>>(p);
+  p.seg.wide = wide_tiling(a->num_windows, kNoAllocItemsPerThread) ? 1 : 0;
+  p.tile_counter = (int32_t*)(scratch + 1);
+  SingleLaunch go{&p, s};
+  go.go<kNoAllocThreads, kNoAllocItemsPerThread>();
   if (cudaGetLastError() != cudaSuccess) return say(a, GATSPI_ECUDA, "kernel launch failed");
   return GATSPI_OK;
 }

@@ -30,19 +30,21 @@ def _levels(nl):
 
 
 def _level0(wl, NW):
-    """Input records for windows 0..NW-1 (one cycle per window)."""
+    """Input records for windows 0..NW-1 (one cycle per window): start,
+    meta (start value in bit 15, edge count below) and the edge times."""
     st, I = wl.stim, wl.netlist.num_inputs
     C = st.num_cycles
-    init = np.zeros(I * NW, np.uint8)
-    off = np.zeros(I * NW, np.int32)
+    start = np.zeros(I * NW, np.int32)
+    meta = np.zeros(I * NW, np.uint16)
     times = []
     for i in range(I):
         for w in range(NW):
             a, b = int(st.edge_ptr[i * C + w]), int(st.edge_ptr[i * C + w + 1])
-            init[i * NW + w] = int(st.init[i]) ^ ((a - int(st.edge_ptr[i * C])) & 1)
-            off[i * NW + w] = len(times)
+            v0 = int(st.init[i]) ^ ((a - int(st.edge_ptr[i * C])) & 1)
+            start[i * NW + w] = len(times)
+            meta[i * NW + w] = (v0 << 15) | (b - a)
             times += st.edge_time[a:b].tolist()
-    return init, off, np.asarray(times, np.int32)
+    return start, meta, np.asarray(times, np.int32)
 
 
 def test_noalloc_levels_match_simulate_twice():
@@ -72,10 +74,10 @@ def test_noalloc_levels_match_simulate_twice():
     gate_delay = t(wl.delays.gate_delay, torch.int32)
     wire_delay = t(wl.delays.wire_delay, torch.int32)
     net_level = t(lv, torch.int32)
-    init0, off0, times0 = _level0(wl, NW)
+    start0, meta0, times0 = _level0(wl, NW)
     capacity = 8 * N * NW + times0.size
-    init = torch.zeros(N * NW, dtype=torch.uint8, device=dev)
-    off = torch.zeros(N * NW + D + 1, dtype=torch.int32, device=dev)
+    rstart = torch.zeros(N * NW, dtype=torch.int32, device=dev)
+    rmeta = torch.zeros(N * NW, dtype=torch.int16, device=dev)
     times = torch.zeros(capacity, dtype=torch.int32, device=dev)
     lvl_base = torch.zeros(D + 2, dtype=torch.int64, device=dev)
     saif_t1 = torch.zeros(N, dtype=torch.int64, device=dev)
@@ -84,9 +86,8 @@ def test_noalloc_levels_match_simulate_twice():
     err = ctypes.create_string_buffer(256)
 
     for run in range(2):
-        init[:I * NW] = t(init0, torch.uint8)
-        off[:I * NW] = t(off0, torch.int32)
-        off[I * NW] = int(times0.size)                 # closes level 0
+        rstart[:I * NW] = t(start0, torch.int32)
+        rmeta[:I * NW] = t(meta0.view(np.int16), torch.int16)
         times[:times0.size] = t(times0, torch.int32)
         lvl_base.zero_()
         lvl_base[1] = int(times0.size)
@@ -97,7 +98,7 @@ def test_noalloc_levels_match_simulate_twice():
         for level in range(1, D + 1):
             a = gs.gatspi_level_args(
                 fanin_ptr.data_ptr(), fanin_net.data_ptr(), lut.data_ptr(), gate_delay.data_ptr(),
-                wire_delay.data_ptr(), net_level.data_ptr(), init.data_ptr(), off.data_ptr(),
+                wire_delay.data_ptr(), net_level.data_ptr(), rstart.data_ptr(), rmeta.data_ptr(),
                 times.data_ptr(), lvl_base.data_ptr(), capacity, saif_t1.data_ptr(),
                 saif_tc.data_ptr(), status.data_ptr(), I, level, gate_begin[level],
                 gate_begin[level + 1], NW, 0, 1, C, wl.stim.cycle_ps, 256, ctypes.cast(err, ctypes.c_char_p))
@@ -112,25 +113,28 @@ def test_noalloc_levels_match_simulate_twice():
         assert np.array_equal(tc[I:], ref_tc[I:]), f"run {run}: TC differs"
         assert np.array_equal(C * wl.stim.cycle_ps - t1[I:], ref_t0[I:])
 
-        h_init, h_off = init.cpu().numpy(), off.cpu().numpy()
+        h_start = rstart.cpu().numpy()
+        h_meta = rmeta.cpu().numpy().view(np.uint16)
         h_times, h_base = times.cpu().numpy(), lvl_base.cpu().numpy()
         for w, (ri, rp, rt) in ref_windows.items():
             for n in range(I, N):
-                it = n * NW + w + lv[n]
-                s, e = int(h_off[it]), int(h_off[it + 1])
-                got = h_times[h_base[lv[n]] + s:h_base[lv[n]] + e].tolist()
-                assert int(h_init[n * NW + w]) == int(ri[n]), f"run {run} window {w} net {n}: start value"
+                r = n * NW + w
+                s, c = int(h_start[r]), int(h_meta[r]) & 0x7FFF
+                b0 = int(h_base[lv[n]])
+                got = h_times[b0 + s:b0 + s + c].tolist()
+                assert int(h_meta[r]) >> 15 == int(ri[n]), f"run {run} window {w} net {n}: start value"
                 assert got == rt[rp[n]:rp[n + 1]].tolist(), f"run {run} window {w} net {n}: edges"
 
 
-def test_noalloc_rejects_levels_beyond_its_scratch():
+def test_noalloc_rejects_levels_beyond_its_limit():
     pytest.importorskip("torch")
     gs.build()
     err = ctypes.create_string_buffer(256)
     dummy = 16  # never dereferenced: the size check comes first
-    a = gs.gatspi_level_args(*([dummy] * 10), 1 << 20, dummy, dummy, dummy, 4, 1, 0, 100,
-                             1 << 21, 0, 1, 1 << 21, 1000, 256,
+    # 4096 gates x 2^20 windows = 2^32 items, beyond GATSPI_NOALLOC_MAX_ITEMS
+    a = gs.gatspi_level_args(*([dummy] * 10), 1 << 20, dummy, dummy, dummy, 4, 1, 0, 4096,
+                             1 << 20, 0, 1, 1 << 20, 1000, 256,
                              ctypes.cast(err, ctypes.c_char_p))
     rc = gs.lib().gatspi_propagate_level_noalloc(ctypes.byref(a), None)
     assert rc == gs.ECAPACITY
-    assert b"GATSPI_NOALLOC_MAX_TILES" in err.value
+    assert b"GATSPI_NOALLOC_MAX_ITEMS" in err.value
