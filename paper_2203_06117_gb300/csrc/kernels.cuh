@@ -347,31 +347,53 @@ __device__ __forceinline__ int32_t simulate_global(const JobView& J, int32_t g, 
   }
 }
 
-// Per-warp shared memory.  Both tilings use the output staging (each lane's
-// column, the compacted tile, per-window edge counts); the gate-aligned
-// tiling also stages, per fanin pin, the windows' record starts, counts and
-// start values and the edge times they cover.
+// Per-warp shared memory.  The linear tiling uses the output staging (each
+// lane's column, the compacted tile, per-item edge counts).  The
+// gate-aligned tiling stages, per fanin pin, the windows' record starts and
+// metas and the edge times they cover, and keeps per window its output meta
+// and offset, plus the list of windows that have fanin edges.
 template <int IPT>
 struct WarpSmem {
   static constexpr int TW = 32 * IPT;    // windows (items) per tile
-  static constexpr int TCAP = 2 * TW;    // edge times staged per pin
-  static constexpr int CAP = 8;          // output edges staged per lane
+  static constexpr int TCAP = TW;        // edge times staged per pin
+  static constexpr int CAP = 8;          // output edges staged per lane (per round)
+  static constexpr int OCAP = (2 * TW > CAP * 32) ? 2 * TW : CAP * 32;  // compacted output edges
   int32_t sstart[4][TW];
   int32_t stimes[4][TCAP];
   int32_t scr[CAP * 32];
-  int32_t cmp[CAP * 32];
-  int32_t cnt[TW];
+  int32_t cmp[OCAP];
+  int32_t cnt[TW];   // linear: per-item edge counts; gate-aligned: per-window output offsets
   uint16_t smeta[4][TW];
+  uint16_t omet[TW];
+  uint8_t list[TW];
 };
 
-// Everything after a tile's simulation: sum the lanes' edge counts with
-// shuffles, take the tile's output range with one atomic add (which also
-// counts the tile done), write the records (start, count and start value of
-// each item), store the edges (compacted through shared memory, or, when a
-// lane's staging column overflowed, by `resim` straight to their final
-// place), and add the SAIF of the lane's last gate.  The level's last tile
-// to take its range publishes the level's edge total as the next level's
-// base; later kernels see it after this launch ends.
+// Takes a tile's output range: one atomic add on the level counter both
+// reserves `aggregate` edges and counts the tile done.  The tile that brings
+// the done count to the level's tile count sees the final edge total and
+// publishes it as the next level's base (later kernels see it after this
+// launch ends).  Returns the range's start relative to the level base (same
+// value in every lane).
+__device__ __forceinline__ long long claim_range(const JobView& J, const SegView& S, int lane, long long aggregate,
+                                                 long long base) {
+  unsigned long long old = 0;
+  if (lane == 0) old = atomicAdd(S.counters, (1ull << kTileShift) + (unsigned long long)aggregate);
+  old = __shfl_sync(0xffffffffu, old, 0);
+  const long long start = (long long)(old & kEdgeMask);
+  if (lane == 0 && (long long)(old >> kTileShift) == (long long)S.n_tiles - 1) {
+    const long long tot = start + aggregate;
+    if (tot > 0x7fffffffll) atomicOr(J.status, kStOffset);
+    J.lvl_base[S.level + 1] = base + tot;
+    if (base + tot > J.capacity) atomicOr(J.status, kStCapacity);
+  }
+  return start;
+}
+
+// Everything after a linear tile's simulation: sum the lanes' edge counts
+// with shuffles, take the tile's output range, write the records (start,
+// count and start value of each item), store the edges (compacted through
+// shared memory, or, when a lane's staging column overflowed, by `resim`
+// straight to their final place), and add the SAIF of the lane's last gate.
 template <int IPT, class Resim>
 __device__ __forceinline__ void finish_tile(const JobView& J, const SegView& S, int lane, WarpSmem<IPT>& sm,
                                             int32_t n_mine, const int32_t* cnt, int32_t total, uint32_t y0s,
@@ -387,17 +409,8 @@ __device__ __forceinline__ void finish_tile(const JobView& J, const SegView& S, 
   }
   const long long excl_l = incl - total;
   const long long aggregate = __shfl_sync(0xffffffffu, incl, 31);
-  unsigned long long old = 0;
-  if (lane == 0) old = atomicAdd(S.counters, (1ull << kTileShift) + (unsigned long long)aggregate);
-  old = __shfl_sync(0xffffffffu, old, 0);
-  const long long start = (long long)(old & kEdgeMask);
   const long long base = __ldg(J.lvl_base + S.level);
-  if (lane == 0 && (long long)(old >> kTileShift) == (long long)S.n_tiles - 1) {
-    const long long tot = start + aggregate;
-    if (tot > 0x7fffffffll) atomicOr(J.status, kStOffset);
-    J.lvl_base[S.level + 1] = base + tot;
-    if (base + tot > J.capacity) atomicOr(J.status, kStCapacity);
-  }
+  const long long start = claim_range(J, S, lane, aggregate, base);
 
   {
     long long o = start + excl_l;
@@ -500,22 +513,31 @@ __device__ __forceinline__ void linear_tile(const JobView& J, const SegView& S, 
 }
 
 // Gate-aligned tiling, K pins: one gate x n <= 32*IPT consecutive windows.
-// The warp first stages, for every pin, the n records and the edge times
-// they cover into shared memory with coalesced loads all in flight
-// together, then each lane simulates its IPT windows reading shared memory
-// only (a pin whose edges exceed the staging room, or are not one
-// contiguous range, is read from global memory instead).
+//  1. The warp stages, for every pin, the n records into shared memory and,
+//     when they cover one run of edge times no longer than TCAP (the case
+//     when the producing tile covered the same windows), those edge times,
+//     all with coalesced loads in flight together.
+//  2. Every window whose pins carry no edge is settled on the spot: its
+//     output is the truth table at the pins' start values, with no edge.
+//     The others are listed, in window order.
+//  3. The listed windows are simulated (Algorithm 1) in rounds of 32, one
+//     per lane, so lanes stay busy however sparse the activity; each round's
+//     edges are compacted, in window order, into the tile's output buffer.
+//  4. One atomic add claims the tile's range; lanes write the records of
+//     consecutive windows and the buffer is stored with coalesced stores.
+//     If some lane's edges did not fit the staging, the listed windows are
+//     simulated again straight into their final place instead.
 template <int K, int IPT>
 __device__ __forceinline__ void wide_tile_k(const JobView& J, const SegView& S, int32_t gl, int32_t wb,
                                             int32_t n, WarpSmem<IPT>& sm) {
   constexpr int CAP = WarpSmem<IPT>::CAP;
   constexpr int TCAP = WarpSmem<IPT>::TCAP;
+  constexpr int OCAP = WarpSmem<IPT>::OCAP;
   const int lane = threadIdx.x & 31;
   const int32_t g = S.gate_begin + gl;
   const int32_t p0 = __ldg(J.fanin_ptr + g);
   long long base[K];
-  int32_t s0[K], dr[K], df[K];
-  bool staged[K];
+  int32_t s0[K], s1[K], dr[K], df[K];  // s0..s1: staged edge range of the pin (empty if not staged)
 #pragma unroll
   for (int i = 0; i < K; ++i) {
     const int32_t pp = p0 + i;
@@ -530,56 +552,68 @@ __device__ __forceinline__ void wide_tile_k(const JobView& J, const SegView& S, 
     }
   }
   __syncwarp();
-  // a pin's edges for these windows are one range when each record starts
-  // where the previous one ends (records of one producing tile); stage the
-  // range then, else read the pin from global memory
 #pragma unroll
   for (int i = 0; i < K; ++i) {
-    bool ok = true;
-    int32_t lo = kInf, hi = 0;
-    for (int j = lane; j < n; j += 32) {
-      const int32_t s = sm.sstart[i][j], c = sm.smeta[i][j] & kMaxCount;
-      if (s < 0 || base[i] + s + c > J.capacity) ok = false;
-      lo = min(lo, s);
-      hi = max(hi, s + c);
-      if (j + 1 < n && sm.sstart[i][j + 1] != s + c) ok = false;
-    }
-#pragma unroll
-    for (int d = 16; d > 0; d >>= 1) {
-      lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, d));
-      hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, d));
-    }
-    ok = __all_sync(0xffffffffu, ok);
-    s0[i] = lo == kInf ? 0 : lo;
-    const int32_t m = hi - s0[i];
-    staged[i] = ok && m >= 0 && m <= TCAP;
-    if (staged[i]) {
-      const int32_t* src = J.times + base[i] + s0[i];
-      for (int j = lane; j < m; j += 32) sm.stimes[i][j] = __ldg(src + j);
+    const int32_t lo = sm.sstart[i][0];
+    const int32_t hi = sm.sstart[i][n - 1] + (int32_t)(sm.smeta[i][n - 1] & (uint32_t)kMaxCount);
+    const bool staged = lo >= 0 && hi >= lo && hi - lo <= TCAP && base[i] + hi <= J.capacity;
+    s0[i] = lo;
+    s1[i] = staged ? hi : lo;
+    if (staged) {
+      const int32_t* src = J.times + base[i] + lo;
+      for (int j = lane; j < hi - lo; j += 32) sm.stimes[i][j] = __ldg(src + j);
     }
   }
   __syncwarp();
   const uint32_t lut = __ldg(J.lut + g);
   const int32_t edit = J.gate_delta ? __ldg(J.gate_delta + g) : 0;
   const int32_t* gd = J.gate_delay + (long long)p0 * 32;
-  const int32_t w_first = lane * IPT;  // this lane's first window inside the tile
-  const int32_t n_mine = max(0, min(IPT, n - w_first));
-  int32_t* cnt = sm.cnt + w_first;
-  int32_t total = 0;
-  uint32_t y0s = 0;
+  const uint32_t lt_mask = (1u << lane) - 1u;
+
+  // 2. settle quiet windows, list the others (window order: k-major, lane-minor)
   long long acc_t1 = 0;
+  int32_t n_act = 0;
+#pragma unroll
+  for (int k = 0; k < IPT; ++k) {
+    const int32_t j = k * 32 + lane;
+    const bool valid = j < n;
+    uint32_t col = 0, any = 0;
+    if (valid) {
+#pragma unroll
+      for (int i = 0; i < K; ++i) {
+        const uint32_t m = sm.smeta[i][j];
+        col |= (m >> 15) << i;
+        any |= m & (uint32_t)kMaxCount;
+      }
+    }
+    const bool act = valid && any != 0u;
+    const uint32_t amask = __ballot_sync(0xffffffffu, act);
+    if (act) {
+      sm.list[n_act + __popc(amask & lt_mask)] = (uint8_t)j;
+    } else if (valid) {
+      const uint32_t y = (lut >> col) & 1u;
+      sm.omet[j] = (uint16_t)(y << 15);
+      if (y) acc_t1 += window_len(J.w0 + wb + j, J.W, J.C, J.L);
+    }
+    n_act += __popc(amask);
+  }
+  __syncwarp();
+
   auto pins_of = [&](int32_t wl, Pin (&pin)[K]) {
 #pragma unroll
     for (int i = 0; i < K; ++i) {
       int32_t s = sm.sstart[i][wl];
       const uint32_t meta = sm.smeta[i][wl];
       int32_t c = (int32_t)(meta & (uint32_t)kMaxCount);
-      if (s < 0 || base[i] + s + c > J.capacity) {  // never read outside the arena
+      // a record's edges come from the staged copy when they lie inside it
+      // (always, when the producing tile covered the same windows)
+      const bool in_stage = s >= s0[i] && s + c <= s1[i];
+      if (!in_stage && (s < 0 || base[i] + s + c > J.capacity)) {  // never read outside the arena
         atomicOr(J.status, kStCorrupt);
         s = 0;
         c = 0;
       }
-      pin[i].t = staged[i] ? &sm.stimes[i][s - s0[i]] : J.times + base[i] + s;
+      pin[i].t = in_stage ? &sm.stimes[i][s - s0[i]] : J.times + base[i] + s;
       pin[i].n = c;
       pin[i].j = 0;
       pin[i].a = kInf;
@@ -588,34 +622,99 @@ __device__ __forceinline__ void wide_tile_k(const JobView& J, const SegView& S, 
       pin[i].v0 = meta >> 15;
     }
   };
-  for (int m = 0; m < n_mine; ++m) {
-    const int32_t wl = w_first + m;
-    Pin pin[K];
-    pins_of(wl, pin);
-    WarpSink<CAP> sink{sm.scr + lane, total};
-    int32_t c = 0, t1 = 0;
-    uint32_t y0 = 0;
-    run_gate<K>(pin, lut, gd, edit, window_len(J.w0 + wb + wl, J.W, J.C, J.L), sink, c, t1, y0);
-    cnt[m] = c;
-    total += c;
-    y0s |= y0 << m;
-    acc_t1 += t1;
+
+  // 3. listed windows, 32 per round, compacted in window order into cmp
+  int32_t out_n = 0;    // the tile's edges so far
+  bool spill = false;   // some round did not fit the staging (warp-uniform)
+  for (int32_t r0 = 0; r0 < n_act; r0 += 32) {
+    const int32_t q = r0 + lane;
+    int32_t c = 0;
+    if (q < n_act) {
+      const int32_t wl = sm.list[q];
+      Pin pin[K];
+      pins_of(wl, pin);
+      WarpSink<CAP> sink{sm.scr + lane, 0};
+      int32_t t1 = 0;
+      uint32_t y0 = 0;
+      run_gate<K>(pin, lut, gd, edit, window_len(J.w0 + wb + wl, J.W, J.C, J.L), sink, c, t1, y0);
+      acc_t1 += t1;
+      sm.omet[wl] = (uint16_t)(min(c, kMaxCount) | (int32_t)(y0 << 15));
+      if (c > kMaxCount) atomicOr(J.status, kStOffset);
+    }
+    int32_t incl = c;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const int32_t v = __shfl_up_sync(0xffffffffu, incl, d);
+      if (lane >= d) incl += v;
+    }
+    const int32_t round_n = __shfl_sync(0xffffffffu, incl, 31);
+    const bool over = __any_sync(0xffffffffu, c > CAP);  // every lane votes
+    spill = spill || over || out_n + round_n > OCAP;
+    if (!spill) {
+      const int32_t at = out_n + incl - c;
+      for (int e = 0; e < c; ++e) sm.cmp[at + e] = sm.scr[e * 32 + lane];
+    }
+    out_n += round_n;
   }
-  const long long rec_first = ((long long)J.I + g) * J.NW + wb + w_first;
-  finish_tile<IPT>(J, S, lane, sm, n_mine, cnt, total, y0s, rec_first, n_mine > 0 ? gl : -1, acc_t1, total,
-                   [&](int32_t* dst, long long o, long long room) {
-                     for (int m = 0; m < n_mine; ++m) {
-                       const int32_t wl = w_first + m;
-                       Pin pin[K];
-                       pins_of(wl, pin);
-                       GlobalSink sink{dst + o, room - o};
-                       int32_t c = 0, t1 = 0;
-                       uint32_t y0 = 0;
-                       run_gate<K>(pin, lut, gd, edit, window_len(J.w0 + wb + wl, J.W, J.C, J.L), sink, c,
-                                   t1, y0);
-                       o += c;
-                     }
-                   });
+  __syncwarp();
+
+  // 4. claim the range; records of consecutive windows per lane
+  const long long lbase = __ldg(J.lvl_base + S.level);
+  const long long start = claim_range(J, S, lane, out_n, lbase);
+  {
+    const int32_t w_first = lane * IPT;
+    int32_t mine = 0;
+#pragma unroll
+    for (int k = 0; k < IPT; ++k)
+      if (w_first + k < n) mine += sm.omet[w_first + k] & kMaxCount;
+    int32_t incl = mine;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const int32_t v = __shfl_up_sync(0xffffffffu, incl, d);
+      if (lane >= d) incl += v;
+    }
+    int32_t o = incl - mine;  // tile-relative
+    const long long rec0 = ((long long)J.I + g) * J.NW + wb;
+#pragma unroll
+    for (int k = 0; k < IPT; ++k) {
+      const int32_t wl = w_first + k;
+      if (wl < n) {
+        const uint16_t m = sm.omet[wl];
+        J.rstart[rec0 + wl] = (int32_t)(start + o);
+        J.rmeta[rec0 + wl] = m;
+        sm.cnt[wl] = o;
+        o += m & kMaxCount;
+      }
+    }
+    if (lane == 31 && start + out_n > 0x7fffffffll) atomicOr(J.status, kStOffset);
+  }
+  int32_t* dst = J.times + lbase + start;
+  const long long room = J.capacity - lbase - start;  // elements left in the arena
+  if (!spill) {
+    const long long m = out_n < room ? out_n : (room > 0 ? room : 0);
+    for (long long e = lane; e < m; e += 32) dst[e] = sm.cmp[e];
+  } else {
+    __syncwarp();
+    for (int32_t q = lane; q < n_act; q += 32) {
+      const int32_t wl = sm.list[q];
+      const int32_t o = sm.cnt[wl];
+      Pin pin[K];
+      pins_of(wl, pin);
+      GlobalSink sink{dst + o, room - o};
+      int32_t c = 0, t1 = 0;
+      uint32_t y0 = 0;
+      run_gate<K>(pin, lut, gd, edit, window_len(J.w0 + wb + wl, J.W, J.C, J.L), sink, c, t1, y0);
+    }
+  }
+
+  // SAIF of the gate: one atomic per tile
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) acc_t1 += __shfl_xor_sync(0xffffffffu, acc_t1, d);
+  if (lane == 0) {
+    const long long net = (long long)J.I + g;
+    if (acc_t1) atomicAdd(J.saif_t1 + net, (unsigned long long)acc_t1);
+    if (out_n) atomicAdd(J.saif_tc + net, (unsigned long long)out_n);
+  }
 }
 
 template <int IPT>
