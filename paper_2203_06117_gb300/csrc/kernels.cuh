@@ -739,14 +739,23 @@ __device__ __forceinline__ void propagate_warp(const JobView& J, const SegView& 
   else linear_tile<IPT>(J, S, tile, sm);
 }
 
-// at most 64 registers per thread: 1024 resident threads per SM
-template <int NT>
-__host__ __device__ constexpr int min_blocks() { return 1024 / NT; }
+// Blocks per SM the launch bounds ask for: as many as the per-warp shared
+// memory lets reside (227 KB per SM), capped at 1024 threads (64 registers
+// per thread).  Where shared memory is the tighter limit, the threads get the
+// registers that limit frees.
+template <int NT, int IPT>
+__host__ __device__ constexpr int smem_blocks() {
+  return (int)((227u * 1024u) / (sizeof(WarpSmem<IPT>) * (NT / 32) + 2048u));
+}
+template <int NT, int IPT>
+__host__ __device__ constexpr int min_blocks() {
+  return smem_blocks<NT, IPT>() < 1 ? 1 : (smem_blocks<NT, IPT>() < 1024 / NT ? smem_blocks<NT, IPT>() : 1024 / NT);
+}
 
 // One level of one job; each warp takes one tile (one atomic per block hands
 // out NT/32 consecutive tiles).
 template <int NT, int IPT>
-__global__ void __launch_bounds__(NT, min_blocks<NT>()) propagate_kernel(const __grid_constant__ PropParams p) {
+__global__ void __launch_bounds__(NT, (min_blocks<NT, IPT>())) propagate_kernel(const __grid_constant__ PropParams p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   WarpSmem<IPT>* sm = reinterpret_cast<WarpSmem<IPT>*>(smem_raw);
   __shared__ int32_t s_first;
@@ -761,7 +770,7 @@ __global__ void __launch_bounds__(NT, min_blocks<NT>()) propagate_kernel(const _
 // as above and mapped to (job, level) segments, each segment with its own
 // counters and tiling.
 template <int NT, int IPT>
-__global__ void __launch_bounds__(NT, min_blocks<NT>()) propagate_multi_kernel(const __grid_constant__ MultiParams m) {
+__global__ void __launch_bounds__(NT, (min_blocks<NT, IPT>())) propagate_multi_kernel(const __grid_constant__ MultiParams m) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   WarpSmem<IPT>* sm = reinterpret_cast<WarpSmem<IPT>*>(smem_raw);
   __shared__ JobView s_job[NT / 32];
