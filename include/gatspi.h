@@ -319,13 +319,20 @@ int gatspi_engine_get_stats(gatspi_engine* eng, gatspi_engine_stats* out);
  *     fanin_ptr/fanin_net/lut/gate_delay/wire_delay are as in
  *     gatspi_load_netlist / gatspi_load_delays (fanin nets in this order);
  *     net_level[n] is the level of net n (inputs 0);
- *   - rstart[n*NW + w] (int32): first edge of (net n, window w), relative
- *     to lvl_base[level(n)];
  *   - rmeta[n*NW + w] (uint16): bit 15 the value of net n at the start of
  *     window w, bits 0-14 its number of edges in the window;
- *   - times[lvl_base[l] + rstart ...] (int32): window-relative edge times,
+ *   - where the edges of (n, w) start, relative to lvl_base[level(n)]:
+ *     with NW >= 64 the kernel works on tiles of one gate x 128 windows and
+ *     tile_info[2*(n*T + t)], tile_info[2*(n*T + t) + 1] (int32, 8-byte
+ *     aligned, T =
+ *     ceil(NW / 128)) are the first edge and the edge count of tile t of
+ *     net n, whose edges are one run in window order, so window w starts at
+ *     its tile's first edge plus the counts of the tile's earlier windows
+ *     (rstart is unused and may be NULL); with fewer windows, rstart[n*NW +
+ *     w] (int32) is the first edge of (n, w) (tile_info may be NULL);
+ *   - times[lvl_base[l] + ...] (int32): window-relative edge times,
  *     `capacity` elements in all; lvl_base (int64, D+2 entries).  A level's
- *     records may appear in any order inside its range of times;
+ *     tiles may appear in any order inside its range of times;
  *   - saif_t1 / saif_tc (uint64 [N]): time at 1 and toggle count, added to;
  *   - status (int32): error bits are ORed in (1 capacity, 2 wait timeout,
  *     4 corrupt record, 8 offset overflow: a level's edges beyond int32 or
@@ -354,6 +361,7 @@ typedef struct gatspi_level_args {
   const int32_t* wire_delay;
   const int32_t* net_level;
   int32_t* rstart;
+  int32_t* tile_info;
   uint16_t* rmeta;
   int32_t* times;
   int64_t* lvl_base;

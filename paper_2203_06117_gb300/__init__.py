@@ -103,7 +103,7 @@ class gatspi_engine_stats(ctypes.Structure):
 class gatspi_level_args(ctypes.Structure):
     """Arguments of gatspi_propagate_level_noalloc (device pointers as ints)."""
     _fields_ = [(n, ctypes.c_void_p) for n in ("fanin_ptr", "fanin_net", "lut", "gate_delay",
-                                                 "wire_delay", "net_level", "rstart", "rmeta", "times",
+                                                 "wire_delay", "net_level", "rstart", "tile_info", "rmeta", "times",
                                                  "lvl_base")] + \
                [("capacity", ctypes.c_int64)] + \
                [(n, ctypes.c_void_p) for n in ("saif_t1", "saif_tc", "status")] + \

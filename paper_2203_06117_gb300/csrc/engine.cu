@@ -30,6 +30,7 @@ struct ENetlist {
   int32_t* d_fanin_ptr = nullptr;
   int32_t* d_fanin_net = nullptr;
   int32_t* d_net_level = nullptr;
+  int32_t* d_gate_desc = nullptr;
   int32_t* d_gate_delay = nullptr;
   int32_t* d_wire_delay = nullptr;
   uint16_t* d_lut = nullptr;
@@ -65,7 +66,9 @@ struct EPart {
   int64_t edge_hint = 0;
   char* mem = nullptr;
   size_t bytes = 0;
-  int32_t* rstart = nullptr;
+  int32_t* rstart = nullptr;  // linear tiling
+  int2* tinfo = nullptr;      // gate-aligned tiling
+  int32_t T = 0, TW = 0;      // tiles per net and windows per tile (gate-aligned), or 0
   uint16_t* rmeta = nullptr;
   int32_t* times = nullptr;
   long long cap = 0;
@@ -155,10 +158,13 @@ void dfree_async(T*& p, cudaStream_t s) {
 }
 
 // Lay out one part's device memory; returns the total bytes.
-size_t part_layout(const ENetlist& nl, EPart& p, char* base) {
+size_t part_layout(const ENetlist& nl, EPart& p, int ipt, char* base) {
   const int64_t N = nl.r.N, D = nl.r.D, NW = p.nw;
+  const bool wide = wide_tiling(p.nw, ipt);
+  const int32_t TW = tile_items_of(ipt);
+  const int32_t T = wide ? (p.nw + TW - 1) / TW : 0;
   int64_t o = 0;
-  const int64_t o_start = o; o = align_up(o + N * NW * 4);
+  const int64_t o_start = o; o = align_up(o + (wide ? N * T * 8 : N * NW * 4));
   const int64_t o_meta = o; o = align_up(o + N * NW * 2);
   const int64_t o_lvl = o; o = align_up(o + (D + 2) * 8);
   // zeroed region: level counters, status, part SAIF
@@ -170,7 +176,10 @@ size_t part_layout(const ENetlist& nl, EPart& p, char* base) {
   const int64_t zero_end = o;
   const int64_t o_times = o; o = align_up(o + p.edge_hint * 4);
   if (base) {
-    p.rstart = (int32_t*)(base + o_start);
+    p.rstart = wide ? nullptr : (int32_t*)(base + o_start);
+    p.tinfo = wide ? (int2*)(base + o_start) : nullptr;
+    p.T = T;
+    p.TW = wide ? TW : 0;
     p.rmeta = (uint16_t*)(base + o_meta);
     p.lvl_base = (long long*)(base + o_lvl);
     p.counters = (unsigned long long*)(base + o_cnt);
@@ -189,8 +198,9 @@ JobView make_view(const ENetlist& nl, const EJob& j, const EPart& p) {
   JobView v{};
   v.fanin_ptr = nl.d_fanin_ptr; v.fanin_net = nl.d_fanin_net; v.lut = nl.d_lut;
   v.gate_delay = nl.d_gate_delay; v.wire_delay = nl.d_wire_delay; v.net_level = nl.d_net_level;
+  v.gdesc = (const int4*)nl.d_gate_desc;
   v.gate_delta = j.d_gate_delta;
-  v.rstart = p.rstart; v.rmeta = p.rmeta; v.times = p.times; v.lvl_base = p.lvl_base; v.capacity = p.cap;
+  v.rstart = p.rstart; v.tinfo = p.tinfo; v.T = p.T; v.rmeta = p.rmeta; v.times = p.times; v.lvl_base = p.lvl_base; v.capacity = p.cap;
   v.saif_t1 = p.t1; v.saif_tc = p.tc; v.status = p.status;
   v.I = nl.r.I; v.NW = p.nw; v.w0 = p.w0; v.W = j.W; v.C = j.C; v.L = j.L;
   return v;
@@ -370,7 +380,7 @@ int gatspi_engine_destroy(gatspi_engine* eng) {
   for (auto& kv : eng->jobs) free_job_device(*kv.second, eng->stream);
   if (eng->stream) cudaStreamSynchronize(eng->stream);
   for (auto& nl : eng->nets) {
-    dfree(nl->d_fanin_ptr); dfree(nl->d_fanin_net); dfree(nl->d_net_level);
+    dfree(nl->d_fanin_ptr); dfree(nl->d_fanin_net); dfree(nl->d_net_level); dfree(nl->d_gate_desc);
     dfree(nl->d_gate_delay); dfree(nl->d_wire_delay); dfree(nl->d_lut);
   }
   for (int k = 0; k < gatspi_engine::kRing; ++k) {
@@ -407,6 +417,9 @@ int gatspi_engine_add_netlist(gatspi_engine* eng, int32_t num_inputs, int32_t nu
   if ((rc = eupload(eng, nl->d_fanin_net, nl->r.fanin_net.data(), nl->r.fanin_net.size()))) return rc;
   if ((rc = eupload(eng, nl->d_net_level, nl->r.net_level.data(), nl->r.net_level.size()))) return rc;
   if ((rc = eupload(eng, nl->d_lut, nl->r.lut.data(), nl->r.lut.size()))) return rc;
+  if (!nl->r.gate_desc.empty() &&
+      (rc = eupload(eng, nl->d_gate_desc, nl->r.gate_desc.data(), nl->r.gate_desc.size())))
+    return rc;
   if ((rc = eupload(eng, nl->d_gate_delay, gd.data(), gd.size()))) return rc;
   if ((rc = eupload(eng, nl->d_wire_delay, wd.data(), wd.size()))) return rc;
   *netlist_id = (int32_t)eng->nets.size();
@@ -511,7 +524,7 @@ int gatspi_engine_step(gatspi_engine* eng, int32_t* active_out, int32_t* queued_
         l0 += j.edge_ptr[(size_t)i * j.C + c1] - j.edge_ptr[(size_t)i * j.C + c0];
       p.edge_hint = l0 + (int64_t)(nl.edges_per_item * (double)nl.r.G * p.nw * 1.25) + 4096;
     }
-    const size_t bytes = part_layout(nl, p, nullptr);
+    const size_t bytes = part_layout(nl, p, eng->ipt, nullptr);
     if (bytes > eng->budget) {
       if (p.nw > 1) {  // split and retry
         std::unique_ptr<EPart> b(new EPart());
@@ -535,7 +548,7 @@ int gatspi_engine_step(gatspi_engine* eng, int32_t* active_out, int32_t* queued_
     eng->queued.pop_front();
     own->mem = (char*)mem;
     own->bytes = bytes;
-    part_layout(nl, *own, own->mem);
+    part_layout(nl, *own, eng->ipt, own->mem);
     eng->in_use += bytes;
     eng->stats.bytes_peak = std::max<int64_t>(eng->stats.bytes_peak, (int64_t)eng->in_use);
     ECK(cudaMemsetAsync(own->mem + own->zero_off, 0, own->zero_bytes, eng->stream));
@@ -590,7 +603,6 @@ int gatspi_engine_step(gatspi_engine* eng, int32_t* active_out, int32_t* queued_
     s.seg.gate_begin = nl.r.lvl_gate_begin[l];
     s.seg.n_items = (nl.r.lvl_gate_begin[l + 1] - nl.r.lvl_gate_begin[l]) * p->nw;
     s.seg.n_tiles = (int32_t)level_tiles(nl.r.lvl_gate_begin[l + 1] - nl.r.lvl_gate_begin[l], p->nw, eng->ipt);
-    s.seg.wide = wide_tiling(p->nw, eng->ipt) ? 1 : 0;
     s.job = (int32_t)views.size();
     s.tile_begin = (int32_t)tiles;
     tiles += s.seg.n_tiles;
@@ -627,7 +639,7 @@ int gatspi_engine_step(gatspi_engine* eng, int32_t* active_out, int32_t* queued_
     InputParams q{};
     q.edge_ptr = j.d_edge_ptr; q.edge_time = j.d_edge_time; q.init_in = j.d_init_in;
     q.in_prefix = (const long long*)(eng->d_stage + pre_off[k]);
-    q.rstart = p.rstart; q.rmeta = p.rmeta; q.times = p.times; q.saif_t1 = p.t1; q.saif_tc = p.tc;
+    q.rstart = p.rstart; q.tinfo = p.tinfo; q.T = p.T; q.TW = p.TW; q.rmeta = p.rmeta; q.times = p.times; q.saif_t1 = p.t1; q.saif_tc = p.tc;
     q.lvl_base = p.lvl_base; q.status = p.status;
     long long l0 = 0;
     const int32_t c0 = p.w0 * j.W, c1 = std::min((p.w0 + p.nw) * j.W, j.C);

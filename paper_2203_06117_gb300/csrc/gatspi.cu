@@ -46,6 +46,7 @@ struct gatspi_ctx {
   int32_t* d_fanin_ptr = nullptr;
   int32_t* d_fanin_net = nullptr;
   int32_t* d_net_level = nullptr;
+  int32_t* d_gate_desc = nullptr;
   uint16_t* d_lut = nullptr;
   int32_t* d_gate_delay = nullptr;
   int32_t* d_wire_delay = nullptr;
@@ -71,7 +72,9 @@ struct gatspi_ctx {
   char* d_arena = nullptr;
   size_t arena_bytes = 0;
   int64_t times_cap_hint = 0;
-  int32_t* d_rstart = nullptr;
+  int32_t* d_rstart = nullptr;  // linear tiling
+  int2* d_tinfo = nullptr;      // gate-aligned tiling
+  int32_t batch_T = 0, batch_TW = 0;
   uint16_t* d_rmeta = nullptr;
   unsigned long long* d_counters = nullptr;  // per level: packed tiles done / edges allocated
   int32_t* d_tile_counter = nullptr;
@@ -120,6 +123,7 @@ void free_netlist(gatspi_ctx* c) {
   dfree(c->d_gate_delta);
   c->max_edit = 0;
   dfree(c->d_fanin_ptr); dfree(c->d_fanin_net); dfree(c->d_net_level); dfree(c->d_lut);
+  dfree(c->d_gate_desc);
   dfree(c->d_gate_delay); dfree(c->d_wire_delay); dfree(c->d_t1); dfree(c->d_tc);
   dfree(c->d_in_prefix);
 }
@@ -134,10 +138,13 @@ void free_arena(gatspi_ctx* c) {
 }
 
 // Carve the arena for a batch of NW windows; returns false if it does not fit.
-bool plan_batch(gatspi_ctx* c, int32_t NW, size_t* need_fixed) {
+bool plan_batch(gatspi_ctx* c, int32_t NW, int ipt, size_t* need_fixed) {
   const int64_t N = c->N;
+  const bool wide = wide_tiling(NW, ipt);
+  const int32_t TW = tile_items_of(ipt);
+  const int32_t T = wide ? (NW + TW - 1) / TW : 0;
   int64_t off = 0;
-  const int64_t o_start = off; off = align_up(off + N * NW * 4);
+  const int64_t o_start = off; off = align_up(off + (wide ? N * T * 8 : N * NW * 4));
   const int64_t o_meta = off; off = align_up(off + N * NW * 2);
   const int64_t o_lvl = off; off = align_up(off + (c->D + 2) * 8);
   const int64_t o_scr = off;
@@ -148,7 +155,10 @@ bool plan_batch(gatspi_ctx* c, int32_t NW, size_t* need_fixed) {
   *need_fixed = (size_t)o_times;
   if ((size_t)o_times + 1024 * 4 > c->arena_bytes) return false;
   char* a = c->d_arena;
-  c->d_rstart = (int32_t*)(a + o_start);
+  c->d_rstart = wide ? nullptr : (int32_t*)(a + o_start);
+  c->d_tinfo = wide ? (int2*)(a + o_start) : nullptr;
+  c->batch_T = T;
+  c->batch_TW = wide ? TW : 0;
   c->d_rmeta = (uint16_t*)(a + o_meta);
   c->d_lvl_base = (long long*)(a + o_lvl);
   c->d_counters = (unsigned long long*)(a + o_scr);
@@ -174,9 +184,11 @@ int ensure_arena(gatspi_ctx* ctx, size_t bytes) {
 }
 
 // Fixed bytes (everything but edge times) for NW windows.
-size_t fixed_bytes(const gatspi_ctx* c, int32_t NW) {
+size_t fixed_bytes(const gatspi_ctx* c, int32_t NW, int ipt) {
   const int64_t N = c->N;
-  return (size_t)(align_up(N * NW * 4) + align_up(N * NW * 2) + align_up((c->D + 2) * 8) +
+  const int32_t TW = tile_items_of(ipt);
+  const int64_t T = (NW + TW - 1) / TW;
+  return (size_t)(align_up(wide_tiling(NW, ipt) ? N * T * 8 : N * NW * 4) + align_up(N * NW * 2) + align_up((c->D + 2) * 8) +
                   align_up((int64_t)(c->D + 2) * 8) + align_up((c->D + 2) * 4) + 4096);
 }
 
@@ -246,6 +258,11 @@ int gatspi_load_netlist(gatspi_ctx* ctx, int32_t num_inputs, int32_t num_gates,
   ctx->lvl_gate_begin = std::move(r.lvl_gate_begin);
   ctx->fanout = std::move(r.fanout);
   int rc;
+  if (!r.gate_desc.empty()) {
+    if ((rc = upload(ctx, ctx->d_gate_desc, r.gate_desc.data(), r.gate_desc.size()))) return rc;
+  } else {
+    dfree(ctx->d_gate_desc);
+  }
   if ((rc = upload(ctx, ctx->d_fanin_ptr, ctx->fanin_ptr.data(), ctx->fanin_ptr.size()))) return rc;
   if ((rc = upload(ctx, ctx->d_fanin_net, ctx->fanin_net.data(), ctx->fanin_net.size()))) return rc;
   if ((rc = upload(ctx, ctx->d_net_level, ctx->net_level.data(), ctx->net_level.size()))) return rc;
@@ -390,9 +407,9 @@ int simulate_impl(gatspi_ctx* ctx, const gatspi_opts* opts) {
   auto want_bytes = [&](int32_t nw) {
     const int64_t items = (int64_t)ctx->N * nw;
     int64_t edges = std::max<int64_t>(ctx->times_cap_hint, items * 2 + (1 << 20));
-    return fixed_bytes(ctx, nw) + (size_t)edges * 4;
+    return fixed_bytes(ctx, nw, ipt) + (size_t)edges * 4;
   };
-  while (NW > 1 && fixed_bytes(ctx, NW) * 2 > ctx->arena_limit) NW = (NW + 1) / 2;
+  while (NW > 1 && fixed_bytes(ctx, NW, ipt) * 2 > ctx->arena_limit) NW = (NW + 1) / 2;
 
   int32_t w0 = 0;
   int64_t edges_total = 0;
@@ -401,7 +418,7 @@ int simulate_impl(gatspi_ctx* ctx, const gatspi_opts* opts) {
     int rc = ensure_arena(ctx, want_bytes(nw));
     if (rc) return rc;
     size_t fixed = 0;
-    if (!plan_batch(ctx, nw, &fixed)) {
+    if (!plan_batch(ctx, nw, ipt, &fixed)) {
       if (NW == 1) return fail(ctx, GATSPI_ECAPACITY, "arena too small for one window");
       NW = (NW + 1) / 2;
       continue;
@@ -430,6 +447,7 @@ int simulate_impl(gatspi_ctx* ctx, const gatspi_opts* opts) {
       InputParams q{};
       q.edge_ptr = ctx->d_edge_ptr; q.edge_time = ctx->d_edge_time; q.init_in = ctx->d_init_in;
       q.in_prefix = ctx->d_in_prefix; q.rstart = ctx->d_rstart; q.rmeta = ctx->d_rmeta; q.times = ctx->d_times;
+      q.tinfo = ctx->d_tinfo; q.T = ctx->batch_T; q.TW = ctx->batch_TW;
       q.saif_t1 = ctx->d_t1; q.saif_tc = ctx->d_tc; q.total = l0; q.lvl_base = ctx->d_lvl_base;
       q.status = ctx->d_status;
       q.I = ctx->I; q.NW = nw; q.w0 = w0; q.W = W; q.C = ctx->C; q.L = ctx->L;
@@ -444,7 +462,8 @@ int simulate_impl(gatspi_ctx* ctx, const gatspi_opts* opts) {
     job.fanin_ptr = ctx->d_fanin_ptr; job.fanin_net = ctx->d_fanin_net; job.lut = ctx->d_lut;
     job.gate_delay = ctx->d_gate_delay; job.wire_delay = ctx->d_wire_delay;
     job.net_level = ctx->d_net_level; job.gate_delta = ctx->d_gate_delta;
-    job.rstart = ctx->d_rstart; job.rmeta = ctx->d_rmeta; job.times = ctx->d_times; job.lvl_base = ctx->d_lvl_base;
+    job.gdesc = (const int4*)ctx->d_gate_desc;
+    job.rstart = ctx->d_rstart; job.tinfo = ctx->d_tinfo; job.T = ctx->batch_T; job.rmeta = ctx->d_rmeta; job.times = ctx->d_times; job.lvl_base = ctx->d_lvl_base;
     job.capacity = ctx->times_cap; job.saif_t1 = ctx->d_t1; job.saif_tc = ctx->d_tc;
     job.status = ctx->d_status;
     job.I = ctx->I; job.NW = nw; job.w0 = w0; job.W = W; job.C = ctx->C; job.L = ctx->L;
@@ -456,7 +475,6 @@ int simulate_impl(gatspi_ctx* ctx, const gatspi_opts* opts) {
       p.seg.gate_begin = ctx->lvl_gate_begin[l];
       p.seg.n_items = (ctx->lvl_gate_begin[l + 1] - ctx->lvl_gate_begin[l]) * nw;
       p.seg.n_tiles = (int32_t)level_tiles(ctx->lvl_gate_begin[l + 1] - ctx->lvl_gate_begin[l], nw, ipt);
-      p.seg.wide = wide_tiling(nw, ipt) ? 1 : 0;
       p.tile_counter = ctx->d_tile_counter + l;
       if (o.time_kernels) CK(cudaEventRecord(ctx->ev[2 * l], ctx->stream));
       SingleLaunch go{&p, ctx->stream};
@@ -674,7 +692,8 @@ int gatspi_read_window(gatspi_ctx* ctx, int32_t window, uint8_t* init, int64_t* 
       break;
     }
     window_gather_kernel<<<(N + 255) / 256, 256, 0, ctx->stream>>>(N, ctx->batch_nw, w, ctx->d_net_level,
-                                                                   ctx->d_rstart, ctx->d_rmeta, ctx->d_lvl_base,
+                                                                   ctx->d_rstart, ctx->d_tinfo, ctx->batch_T,
+                                                                   ctx->batch_TW, ctx->d_rmeta, ctx->d_lvl_base,
                                                                    ctx->d_times, d_dst, d_out);
     if (cudaMemcpyAsync(times, d_out, sizeof(int32_t) * tot, cudaMemcpyDeviceToHost, ctx->stream) ||
         cudaStreamSynchronize(ctx->stream)) {

@@ -29,6 +29,11 @@ struct Prepared {
   std::vector<int32_t> lvl_gate_begin;  // [D+2]: level l >= 1 holds internal
                                         // gates lvl_gate_begin[l] .. [l+1]
   std::vector<int64_t> fanout;          // pins driven by each internal net
+  // Per internal gate, 8 words the propagation kernel fetches in one go:
+  // fanin nets (unused pins repeat pin 0's net), first pin, truth table |
+  // pin count << 16, fanin levels as 16-bit pairs.  Empty when a level
+  // exceeds 65535 (the kernel then reads the CSR arrays).
+  std::vector<int32_t> gate_desc;       // [G*8]
 };
 
 // Validate and levelize.  Returns an empty string on success, else why not.
@@ -92,6 +97,22 @@ inline std::string prepare_netlist(int32_t I, int32_t G, const int32_t* fanin_pt
     }
     r.lut[j] = lut[g];
     r.net_level[(size_t)I + j] = level[(size_t)I + g];
+  }
+  if (D <= 0xffff) {
+    r.gate_desc.assign((size_t)G * 8, 0);
+    for (int32_t j = 0; j < G; ++j) {
+      int32_t* d = &r.gate_desc[(size_t)j * 8];
+      const int32_t p0 = r.fanin_ptr[j], k = r.fanin_ptr[j + 1] - p0;
+      int32_t lv[kMaxPins];
+      for (int i = 0; i < kMaxPins; ++i) {
+        d[i] = r.fanin_net[p0 + (i < k ? i : 0)];
+        lv[i] = r.net_level[d[i]];
+      }
+      d[4] = p0;
+      d[5] = (int32_t)((uint32_t)r.lut[j] | ((uint32_t)k << 16));
+      d[6] = (int32_t)((uint32_t)lv[0] | ((uint32_t)lv[1] << 16));
+      d[7] = (int32_t)((uint32_t)lv[2] | ((uint32_t)lv[3] << 16));
+    }
   }
   return "";
 }

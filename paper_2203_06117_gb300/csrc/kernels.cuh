@@ -11,19 +11,25 @@
 // pass, then a storing pass at the scanned offsets.  Here one pass suffices.
 // A warp stages its items' edges in shared memory, sums its edge count with
 // shuffles, and takes its output range with one atomic add on the level's
-// counter.  Records therefore carry their own start and count, and no tile
-// waits for another.  The same add counts the tile as done (the counter
-// packs tiles done above the edges allocated), so the level's last tile
-// sees the final edge total and publishes it, which places the next level.
+// counter, so no tile waits for another.  The same add counts the tile as
+// done (the counter packs tiles done above the edges allocated), so the
+// level's last tile sees the final edge total and publishes it, which
+// places the next level.
 //
 // Waveform store (one batch of NW windows):
-//   rstart[n*NW + w]  int32   first edge of (net n, window w), relative to
-//                             lvl_base[level(n)]
-//   rmeta[n*NW + w]   uint16  bit 15: value at the window start; bits 0-14:
-//                             edge count
-//   times[lvl_base[level(n)] + rstart ...]  int32 window-relative edge times
-// The records of a net's windows are contiguous, so a warp's record loads
-// for one pin cover one contiguous range.
+//   rmeta[n*NW + w]   uint16  bit 15: value of net n at the start of window
+//                             w; bits 0-14: its edge count in the window
+//   times[lvl_base[level(n)] + ...]  int32 window-relative edge times
+// and where each record's edges start, in one of two forms:
+//   gate-aligned tiling (NW >= 16*IPT): tiles are one gate x TW = 32*IPT
+//     windows, and the edges of a tile are one run in window order;
+//     tinfo[n*T + t] = {first edge relative to lvl_base[level(n)], edges}
+//     for tile t of net n (T = ceil(NW / TW)), and a window's first edge is
+//     its tile's plus the counts of the tile's earlier windows;
+//   linear tiling (fewer windows): rstart[n*NW + w] int32, the first edge of
+//     each record relative to lvl_base[level(n)].
+// A net's records are contiguous, so a warp's record loads for one pin
+// cover one contiguous range.
 #pragma once
 
 #include <cstdint>
@@ -57,8 +63,11 @@ struct JobView {
   const int32_t* __restrict__ wire_delay;  // [P][2]
   const int32_t* __restrict__ net_level;   // [N]
   const int32_t* __restrict__ gate_delta;  // [G] delay edit per gate, or null
+  const int4* __restrict__ gdesc;          // [G][2] gate descriptors, or null (then the CSR arrays)
   // waveform store
-  int32_t* rstart;
+  int32_t* rstart;  // linear tiling: [N*NW] record starts
+  int2* tinfo;      // gate-aligned tiling: [N*T] tile runs
+  int32_t T;        // tiles per net with gate-aligned tiling, 0 with linear
   uint16_t* rmeta;
   int32_t* times;
   long long* lvl_base;  // [D+2]
@@ -81,9 +90,6 @@ struct SegView {
   int32_t gate_begin;  // first internal gate of the level
   int32_t n_items;     // gates of the level * NW
   int32_t n_tiles;
-  int32_t wide;        // 1: tiles of one gate x up to 32*IPT windows, fanin
-                       // waveforms staged in shared memory; 0: tiles of
-                       // 32*IPT consecutive items, fanins read from global
 };
 
 struct PropParams {
@@ -146,7 +152,8 @@ __device__ __forceinline__ void pin_advance(Pin& q) {
   q.a = a;
 }
 
-// Algorithm 1 for one gate and one window (`edit` shifts every gate delay of
+// Algorithm 1 for one gate and one window (`gd`: the gate's delay tables, 32
+// entries per pin, in global or shared memory; `edit` shifts every gate delay of
 // the gate, clamped at 1 ps; 0 without a delay edit).  The output keeps at
 // most one edge that may still be cancelled (the last kept one, `pend`): a
 // cancel needs the last kept edge to lie after the current time, and once an
@@ -197,7 +204,7 @@ __device__ __forceinline__ void run_gate(Pin (&pin)[K], uint32_t lut,
         if (pend_on) flush(pend);
         const uint32_t side = (col & ((1u << istar) - 1u)) | ((col >> (istar + 1)) << istar);
         const uint32_t ie = (col >> istar) & 1u;
-        pend = t + max(1, __ldg(gd + istar * 32 + (int)(ie * 16u + yn * 8u + side)) + edit);
+        pend = t + max(1, gd[istar * 32 + (int)(ie * 16u + yn * 8u + side)] + edit);
         pend_on = true;
       }
       y = yn;
@@ -349,20 +356,22 @@ __device__ __forceinline__ int32_t simulate_global(const JobView& J, int32_t g, 
 
 // Per-warp shared memory.  The linear tiling uses the output staging (each
 // lane's column, the compacted tile, per-item edge counts).  The
-// gate-aligned tiling stages, per fanin pin, the windows' record starts and
-// metas and the edge times they cover, and keeps per window its output meta
-// and offset, plus the list of windows that have fanin edges.
+// gate-aligned tiling stages, per fanin pin, the windows' metas, their edge
+// starts inside the pin's tile run, the run itself (pins share one pool),
+// and the gate's delay tables; and keeps per window its output meta, plus
+// the list of windows that have fanin edges.
 template <int IPT>
 struct WarpSmem {
   static constexpr int TW = 32 * IPT;    // windows (items) per tile
-  static constexpr int TCAP = TW;        // edge times staged per pin
+  static constexpr int POOL = 4 * TW;    // fanin edge times staged per tile
   static constexpr int CAP = 8;          // output edges staged per lane (per round)
   static constexpr int OCAP = (2 * TW > CAP * 32) ? 2 * TW : CAP * 32;  // compacted output edges
   int32_t sstart[4][TW];
-  int32_t stimes[4][TCAP];
+  int32_t spool[POOL];
   int32_t scr[CAP * 32];
   int32_t cmp[OCAP];
-  int32_t cnt[TW];   // linear: per-item edge counts; gate-aligned: per-window output offsets
+  int32_t cnt[TW];     // linear: per-item edge counts; gate-aligned: per-window output offsets
+  int32_t sgd[4][32];  // gate-aligned: the gate's delay tables
   uint16_t smeta[4][TW];
   uint16_t omet[TW];
   uint8_t list[TW];
@@ -512,65 +521,132 @@ __device__ __forceinline__ void linear_tile(const JobView& J, const SegView& S, 
                    });
 }
 
-// Gate-aligned tiling, K pins: one gate x n <= 32*IPT consecutive windows.
-//  1. The warp stages, for every pin, the n records into shared memory and,
-//     when they cover one run of edge times no longer than TCAP (the case
-//     when the producing tile covered the same windows), those edge times,
-//     all with coalesced loads in flight together.
+// A gate's fanin nets and their levels, first pin, truth table and pin
+// count: one 32-byte descriptor, or the CSR arrays when there is none.
+struct GateDesc {
+  int32_t net[4];
+  int32_t lvl[4];
+  int32_t p0, k;
+  uint32_t lut;
+};
+
+__device__ __forceinline__ void load_desc(const JobView& J, int32_t g, GateDesc& d) {
+  if (J.gdesc) {
+    const int4 a = __ldg(J.gdesc + 2 * (long long)g);
+    const int4 b = __ldg(J.gdesc + 2 * (long long)g + 1);
+    d.net[0] = a.x; d.net[1] = a.y; d.net[2] = a.z; d.net[3] = a.w;
+    d.p0 = b.x;
+    d.lut = (uint32_t)b.y & 0xffffu;
+    d.k = (int32_t)((uint32_t)b.y >> 16);
+    d.lvl[0] = (int32_t)((uint32_t)b.z & 0xffffu); d.lvl[1] = (int32_t)((uint32_t)b.z >> 16);
+    d.lvl[2] = (int32_t)((uint32_t)b.w & 0xffffu); d.lvl[3] = (int32_t)((uint32_t)b.w >> 16);
+  } else {
+    d.p0 = __ldg(J.fanin_ptr + g);
+    d.k = __ldg(J.fanin_ptr + g + 1) - d.p0;
+    d.lut = __ldg(J.lut + g);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      d.net[i] = __ldg(J.fanin_net + d.p0 + (i < d.k ? i : 0));
+      d.lvl[i] = __ldg(J.net_level + d.net[i]);
+    }
+  }
+}
+
+// Gate-aligned tiling, K pins: tile tg of gate g, windows wb .. wb+n-1 (n <= TW).
+//  1. Everything that depends on the gate descriptor only is loaded at once:
+//     each pin's level base, tile run, wire and gate delays, and the n metas
+//     (kept in registers).  Then the pins' runs are staged into the pool
+//     (in pin order while they fit), and each pin's per-window edge starts
+//     inside its run are found by a warp scan of its counts.
 //  2. Every window whose pins carry no edge is settled on the spot: its
 //     output is the truth table at the pins' start values, with no edge.
 //     The others are listed, in window order.
 //  3. The listed windows are simulated (Algorithm 1) in rounds of 32, one
 //     per lane, so lanes stay busy however sparse the activity; each round's
 //     edges are compacted, in window order, into the tile's output buffer.
-//  4. One atomic add claims the tile's range; lanes write the records of
-//     consecutive windows and the buffer is stored with coalesced stores.
+//  4. One atomic add claims the tile's run.  The output metas are stored
+//     while it is in flight, then the run (coalesced) and the tile's entry.
 //     If some lane's edges did not fit the staging, the listed windows are
 //     simulated again straight into their final place instead.
 template <int K, int IPT>
-__device__ __forceinline__ void wide_tile_k(const JobView& J, const SegView& S, int32_t gl, int32_t wb,
-                                            int32_t n, WarpSmem<IPT>& sm) {
+__device__ __forceinline__ void wide_tile_k(const JobView& J, const SegView& S, const GateDesc& d, int32_t gl,
+                                            int32_t tg, int32_t n, WarpSmem<IPT>& sm) {
   constexpr int CAP = WarpSmem<IPT>::CAP;
-  constexpr int TCAP = WarpSmem<IPT>::TCAP;
+  constexpr int POOL = WarpSmem<IPT>::POOL;
   constexpr int OCAP = WarpSmem<IPT>::OCAP;
+  constexpr int TW = WarpSmem<IPT>::TW;
   const int lane = threadIdx.x & 31;
   const int32_t g = S.gate_begin + gl;
-  const int32_t p0 = __ldg(J.fanin_ptr + g);
+  const int32_t wb = tg * TW;
+  const int32_t p0 = d.p0;
+
+  // 1. loads that depend on the descriptor only, all in flight together
   long long base[K];
-  int32_t s0[K], s1[K], dr[K], df[K];  // s0..s1: staged edge range of the pin (empty if not staged)
+  int2 run[K];
+  int32_t dr[K], df[K], gdv[K];
+  uint32_t mv[K][IPT];
 #pragma unroll
   for (int i = 0; i < K; ++i) {
     const int32_t pp = p0 + i;
-    const int32_t net = __ldg(J.fanin_net + pp);
-    const long long rec = (long long)net * J.NW + wb;
-    base[i] = __ldg(J.lvl_base + __ldg(J.net_level + net));
+    base[i] = __ldg(J.lvl_base + d.lvl[i]);
+    run[i] = __ldg(J.tinfo + (long long)d.net[i] * J.T + tg);
     dr[i] = __ldg(J.wire_delay + 2 * pp);
     df[i] = __ldg(J.wire_delay + 2 * pp + 1);
-    for (int j = lane; j < n; j += 32) {
-      sm.sstart[i][j] = __ldg(J.rstart + rec + j);
-      sm.smeta[i][j] = __ldg(J.rmeta + rec + j);
+    gdv[i] = __ldg(J.gate_delay + (long long)pp * 32 + lane);
+    const uint16_t* mp = J.rmeta + (long long)d.net[i] * J.NW + wb;
+#pragma unroll
+    for (int k = 0; k < IPT; ++k) mv[i][k] = (k * 32 + lane < n) ? (uint32_t)__ldg(mp + k * 32 + lane) : 0u;
+  }
+  const int32_t edit = J.gate_delta ? __ldg(J.gate_delta + g) : 0;
+
+  // pins' runs into the pool; src[i] + s is where edge s of pin i's run is
+  const int32_t* src[K];
+  int32_t lim[K];  // edges in the pin's run (0 if it failed its bounds check)
+  {
+    int32_t used = 0;
+#pragma unroll
+    for (int i = 0; i < K; ++i) {
+      const int32_t lo = run[i].x, c = run[i].y;
+      const bool ok = lo >= 0 && c >= 0 && base[i] + lo + c <= J.capacity;
+      if (!ok && lane == 0) atomicOr(J.status, kStCorrupt);
+      lim[i] = ok ? c : 0;
+      if (ok && used + c <= POOL) {
+        const int32_t* gsrc = J.times + base[i] + lo;
+        for (int j = lane; j < c; j += 32) sm.spool[used + j] = __ldg(gsrc + j);
+        src[i] = &sm.spool[used];
+        used += c;
+      } else {
+        src[i] = J.times + (ok ? base[i] + lo : 0);
+      }
     }
   }
-  __syncwarp();
 #pragma unroll
   for (int i = 0; i < K; ++i) {
-    const int32_t lo = sm.sstart[i][0];
-    const int32_t hi = sm.sstart[i][n - 1] + (int32_t)(sm.smeta[i][n - 1] & (uint32_t)kMaxCount);
-    const bool staged = lo >= 0 && hi >= lo && hi - lo <= TCAP && base[i] + hi <= J.capacity;
-    s0[i] = lo;
-    s1[i] = staged ? hi : lo;
-    if (staged) {
-      const int32_t* src = J.times + base[i] + lo;
-      for (int j = lane; j < hi - lo; j += 32) sm.stimes[i][j] = __ldg(src + j);
+    sm.sgd[i][lane] = gdv[i];
+#pragma unroll
+    for (int k = 0; k < IPT; ++k)
+      if (k * 32 + lane < n) sm.smeta[i][k * 32 + lane] = (uint16_t)mv[i][k];
+    // edge starts inside the run: exclusive scan of the counts in window order
+    if (lim[i] > 0) {
+      int32_t carry = 0;
+#pragma unroll
+      for (int k = 0; k < IPT; ++k) {
+        const int32_t c = (int32_t)(mv[i][k] & (uint32_t)kMaxCount);
+        int32_t incl = c;
+#pragma unroll
+        for (int dd = 1; dd < 32; dd <<= 1) {
+          const int32_t v = __shfl_up_sync(0xffffffffu, incl, dd);
+          if (lane >= dd) incl += v;
+        }
+        if (k * 32 + lane < n) sm.sstart[i][k * 32 + lane] = carry + incl - c;
+        carry += __shfl_sync(0xffffffffu, incl, 31);
+      }
     }
   }
-  __syncwarp();
-  const uint32_t lut = __ldg(J.lut + g);
-  const int32_t edit = J.gate_delta ? __ldg(J.gate_delta + g) : 0;
-  const int32_t* gd = J.gate_delay + (long long)p0 * 32;
-  const uint32_t lt_mask = (1u << lane) - 1u;
 
   // 2. settle quiet windows, list the others (window order: k-major, lane-minor)
+  const uint32_t lut = d.lut;
+  const uint32_t lt_mask = (1u << lane) - 1u;
   long long acc_t1 = 0;
   int32_t n_act = 0;
 #pragma unroll
@@ -578,13 +654,10 @@ __device__ __forceinline__ void wide_tile_k(const JobView& J, const SegView& S, 
     const int32_t j = k * 32 + lane;
     const bool valid = j < n;
     uint32_t col = 0, any = 0;
-    if (valid) {
 #pragma unroll
-      for (int i = 0; i < K; ++i) {
-        const uint32_t m = sm.smeta[i][j];
-        col |= (m >> 15) << i;
-        any |= m & (uint32_t)kMaxCount;
-      }
+    for (int i = 0; i < K; ++i) {
+      col |= (mv[i][k] >> 15) << i;
+      any |= mv[i][k] & (uint32_t)kMaxCount;
     }
     const bool act = valid && any != 0u;
     const uint32_t amask = __ballot_sync(0xffffffffu, act);
@@ -599,21 +672,19 @@ __device__ __forceinline__ void wide_tile_k(const JobView& J, const SegView& S, 
   }
   __syncwarp();
 
+  const int32_t* gd = &sm.sgd[0][0];
   auto pins_of = [&](int32_t wl, Pin (&pin)[K]) {
 #pragma unroll
     for (int i = 0; i < K; ++i) {
-      int32_t s = sm.sstart[i][wl];
       const uint32_t meta = sm.smeta[i][wl];
       int32_t c = (int32_t)(meta & (uint32_t)kMaxCount);
-      // a record's edges come from the staged copy when they lie inside it
-      // (always, when the producing tile covered the same windows)
-      const bool in_stage = s >= s0[i] && s + c <= s1[i];
-      if (!in_stage && (s < 0 || base[i] + s + c > J.capacity)) {  // never read outside the arena
+      int32_t s = c ? sm.sstart[i][wl] : 0;
+      if (s < 0 || s + c > lim[i]) {  // never read outside the pin's run
         atomicOr(J.status, kStCorrupt);
         s = 0;
         c = 0;
       }
-      pin[i].t = in_stage ? &sm.stimes[i][s - s0[i]] : J.times + base[i] + s;
+      pin[i].t = src[i] + s;
       pin[i].n = c;
       pin[i].j = 0;
       pin[i].a = kInf;
@@ -643,9 +714,9 @@ __device__ __forceinline__ void wide_tile_k(const JobView& J, const SegView& S, 
     }
     int32_t incl = c;
 #pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-      const int32_t v = __shfl_up_sync(0xffffffffu, incl, d);
-      if (lane >= d) incl += v;
+    for (int dd = 1; dd < 32; dd <<= 1) {
+      const int32_t v = __shfl_up_sync(0xffffffffu, incl, dd);
+      if (lane >= dd) incl += v;
     }
     const int32_t round_n = __shfl_sync(0xffffffffu, incl, 31);
     const bool over = __any_sync(0xffffffffu, c > CAP);  // every lane votes
@@ -658,35 +729,27 @@ __device__ __forceinline__ void wide_tile_k(const JobView& J, const SegView& S, 
   }
   __syncwarp();
 
-  // 4. claim the range; records of consecutive windows per lane
+  // 4. claim the run; store the metas while the claim is in flight
   const long long lbase = __ldg(J.lvl_base + S.level);
-  const long long start = claim_range(J, S, lane, out_n, lbase);
+  unsigned long long old = 0;
+  if (lane == 0) old = atomicAdd(S.counters, (1ull << kTileShift) + (unsigned long long)out_n);
   {
-    const int32_t w_first = lane * IPT;
-    int32_t mine = 0;
+    uint16_t* om = J.rmeta + ((long long)J.I + g) * J.NW + wb;
 #pragma unroll
     for (int k = 0; k < IPT; ++k)
-      if (w_first + k < n) mine += sm.omet[w_first + k] & kMaxCount;
-    int32_t incl = mine;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-      const int32_t v = __shfl_up_sync(0xffffffffu, incl, d);
-      if (lane >= d) incl += v;
+      if (k * 32 + lane < n) om[k * 32 + lane] = sm.omet[k * 32 + lane];
+  }
+  old = __shfl_sync(0xffffffffu, old, 0);
+  const long long start = (long long)(old & kEdgeMask);
+  if (lane == 0) {
+    if ((long long)(old >> kTileShift) == (long long)S.n_tiles - 1) {
+      const long long tot = start + out_n;
+      if (tot > 0x7fffffffll) atomicOr(J.status, kStOffset);
+      J.lvl_base[S.level + 1] = lbase + tot;
+      if (lbase + tot > J.capacity) atomicOr(J.status, kStCapacity);
     }
-    int32_t o = incl - mine;  // tile-relative
-    const long long rec0 = ((long long)J.I + g) * J.NW + wb;
-#pragma unroll
-    for (int k = 0; k < IPT; ++k) {
-      const int32_t wl = w_first + k;
-      if (wl < n) {
-        const uint16_t m = sm.omet[wl];
-        J.rstart[rec0 + wl] = (int32_t)(start + o);
-        J.rmeta[rec0 + wl] = m;
-        sm.cnt[wl] = o;
-        o += m & kMaxCount;
-      }
-    }
-    if (lane == 31 && start + out_n > 0x7fffffffll) atomicOr(J.status, kStOffset);
+    if (start + out_n > 0x7fffffffll) atomicOr(J.status, kStOffset);
+    J.tinfo[((long long)J.I + g) * J.T + tg] = make_int2((int32_t)start, out_n);
   }
   int32_t* dst = J.times + lbase + start;
   const long long room = J.capacity - lbase - start;  // elements left in the arena
@@ -694,13 +757,33 @@ __device__ __forceinline__ void wide_tile_k(const JobView& J, const SegView& S, 
     const long long m = out_n < room ? out_n : (room > 0 ? room : 0);
     for (long long e = lane; e < m; e += 32) dst[e] = sm.cmp[e];
   } else {
+    // output offsets of the windows inside the run (consecutive windows per lane)
+    const int32_t w_first = lane * IPT;
+    int32_t mine = 0;
+#pragma unroll
+    for (int k = 0; k < IPT; ++k)
+      if (w_first + k < n) mine += sm.omet[w_first + k] & kMaxCount;
+    int32_t incl = mine;
+#pragma unroll
+    for (int dd = 1; dd < 32; dd <<= 1) {
+      const int32_t v = __shfl_up_sync(0xffffffffu, incl, dd);
+      if (lane >= dd) incl += v;
+    }
+    int32_t o = incl - mine;
+#pragma unroll
+    for (int k = 0; k < IPT; ++k) {
+      if (w_first + k < n) {
+        sm.cnt[w_first + k] = o;
+        o += sm.omet[w_first + k] & kMaxCount;
+      }
+    }
     __syncwarp();
     for (int32_t q = lane; q < n_act; q += 32) {
       const int32_t wl = sm.list[q];
-      const int32_t o = sm.cnt[wl];
+      const int32_t at = sm.cnt[wl];
       Pin pin[K];
       pins_of(wl, pin);
-      GlobalSink sink{dst + o, room - o};
+      GlobalSink sink{dst + at, room - at};
       int32_t c = 0, t1 = 0;
       uint32_t y0 = 0;
       run_gate<K>(pin, lut, gd, edit, window_len(J.w0 + wb + wl, J.W, J.C, J.L), sink, c, t1, y0);
@@ -709,7 +792,7 @@ __device__ __forceinline__ void wide_tile_k(const JobView& J, const SegView& S, 
 
   // SAIF of the gate: one atomic per tile
 #pragma unroll
-  for (int d = 16; d > 0; d >>= 1) acc_t1 += __shfl_xor_sync(0xffffffffu, acc_t1, d);
+  for (int dd = 16; dd > 0; dd >>= 1) acc_t1 += __shfl_xor_sync(0xffffffffu, acc_t1, dd);
   if (lane == 0) {
     const long long net = (long long)J.I + g;
     if (acc_t1) atomicAdd(J.saif_t1 + net, (unsigned long long)acc_t1);
@@ -720,22 +803,22 @@ __device__ __forceinline__ void wide_tile_k(const JobView& J, const SegView& S, 
 template <int IPT>
 __device__ __forceinline__ void wide_tile(const JobView& J, const SegView& S, int32_t tile, WarpSmem<IPT>& sm) {
   constexpr int TW = 32 * IPT;
-  const int32_t tpg = (J.NW + TW - 1) / TW;  // tiles per gate
-  const int32_t gl = tile / tpg;
-  const int32_t wb = (tile - gl * tpg) * TW;
-  const int32_t n = min(TW, J.NW - wb);
-  const int32_t g = S.gate_begin + gl;
-  switch (__ldg(J.fanin_ptr + g + 1) - __ldg(J.fanin_ptr + g)) {
-    case 1: wide_tile_k<1, IPT>(J, S, gl, wb, n, sm); break;
-    case 2: wide_tile_k<2, IPT>(J, S, gl, wb, n, sm); break;
-    case 3: wide_tile_k<3, IPT>(J, S, gl, wb, n, sm); break;
-    default: wide_tile_k<4, IPT>(J, S, gl, wb, n, sm); break;
+  const int32_t gl = tile / J.T;
+  const int32_t tg = tile - gl * J.T;
+  const int32_t n = min(TW, J.NW - tg * TW);
+  GateDesc d;
+  load_desc(J, S.gate_begin + gl, d);
+  switch (d.k) {
+    case 1: wide_tile_k<1, IPT>(J, S, d, gl, tg, n, sm); break;
+    case 2: wide_tile_k<2, IPT>(J, S, d, gl, tg, n, sm); break;
+    case 3: wide_tile_k<3, IPT>(J, S, d, gl, tg, n, sm); break;
+    default: wide_tile_k<4, IPT>(J, S, d, gl, tg, n, sm); break;
   }
 }
 
 template <int IPT>
 __device__ __forceinline__ void propagate_warp(const JobView& J, const SegView& S, int32_t tile, WarpSmem<IPT>& sm) {
-  if (S.wide) wide_tile<IPT>(J, S, tile, sm);
+  if (J.T > 0) wide_tile<IPT>(J, S, tile, sm);
   else linear_tile<IPT>(J, S, tile, sm);
 }
 
@@ -875,7 +958,9 @@ struct InputParams {
   const int32_t* __restrict__ edge_time;
   const uint8_t* __restrict__ init_in;    // [I]
   const long long* __restrict__ in_prefix;  // [I] edges of inputs < i in this batch
-  int32_t* rstart;
+  int32_t* rstart;  // linear tiling
+  int2* tinfo;      // gate-aligned tiling
+  int32_t T, TW;    // tiles per net and windows per tile (gate-aligned), or 0
   uint16_t* rmeta;
   int32_t* times;
   unsigned long long* saif_t1;
@@ -904,7 +989,14 @@ __global__ void inputs_kernel(const InputParams q) {
     const long long o = q.in_prefix[i] + (a - ep[q.w0 * q.W]);
     uint32_t v = (q.init_in[i] ^ (uint32_t)((a - ep[0]) & 1)) & 1u;
     cnt = (int32_t)(b - a);
-    q.rstart[(long long)i * q.NW + w] = (int32_t)o;
+    if (q.T > 0) {
+      if (w % q.TW == 0) {  // the tile's run: its windows' edges, in order
+        const int32_t ct = min((q.w0 + min(w + q.TW, q.NW)) * q.W, q.C);
+        q.tinfo[(long long)i * q.T + w / q.TW] = make_int2((int32_t)o, (int32_t)(ep[ct] - a));
+      }
+    } else {
+      q.rstart[(long long)i * q.NW + w] = (int32_t)o;
+    }
     q.rmeta[(long long)i * q.NW + w] = (uint16_t)(min(cnt, kMaxCount) | (int32_t)(v << 15));
     if (cnt > kMaxCount) atomicOr(q.status, kStOffset);
     const int32_t len = (c1 - c0) * q.L;
@@ -960,13 +1052,21 @@ __global__ void window_counts_kernel(int32_t N, int32_t NW, int32_t w, const uin
 }
 
 __global__ void window_gather_kernel(int32_t N, int32_t NW, int32_t w, const int32_t* net_level,
-                                     const int32_t* rstart, const uint16_t* rmeta, const long long* lvl_base,
-                                     const int32_t* times, const long long* dst_ptr, int32_t* out) {
+                                     const int32_t* rstart, const int2* tinfo, int32_t T, int32_t TW,
+                                     const uint16_t* rmeta, const long long* lvl_base, const int32_t* times,
+                                     const long long* dst_ptr, int32_t* out) {
   const int32_t n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= N) return;
   const long long rec = (long long)n * NW + w;
-  const int32_t s = rstart[rec];
   const int32_t c = (int32_t)(rmeta[rec] & (uint32_t)kMaxCount);
+  long long s;
+  if (T > 0) {  // the tile's run start plus the counts of its earlier windows
+    const int32_t t = w / TW;
+    s = tinfo[(long long)n * T + t].x;
+    for (int32_t v = t * TW; v < w; ++v) s += rmeta[(long long)n * NW + v] & (uint32_t)kMaxCount;
+  } else {
+    s = rstart[rec];
+  }
   const int32_t* src = times + lvl_base[net_level[n]] + s;
   const long long d = dst_ptr[n];
   for (int32_t k = 0; k < c; ++k) out[d + k] = src[k];

@@ -76,7 +76,7 @@ extern "C" int gatspi_propagate_level_noalloc(const gatspi_level_args* a, void* 
   if (!a) return GATSPI_EINVAL;
   if (a->err && a->err_len > 0) a->err[0] = 0;
   if (!a->fanin_ptr || !a->fanin_net || !a->lut || !a->gate_delay || !a->wire_delay || !a->net_level ||
-      !a->rstart || !a->rmeta || !a->times || !a->lvl_base || !a->saif_t1 || !a->saif_tc || !a->status)
+      !a->rmeta || !a->times || !a->lvl_base || !a->saif_t1 || !a->saif_tc || !a->status)
     return say(a, GATSPI_EINVAL, "a device pointer is null");
   if (a->num_inputs < 1 || a->level < 1 || a->gate_begin < 0 || a->gate_end <= a->gate_begin ||
       a->num_windows < 1 || a->first_window < 0 || a->window_cycles < 1 || a->num_cycles < 1 ||
@@ -88,6 +88,12 @@ extern "C" int gatspi_propagate_level_noalloc(const gatspi_level_args* a, void* 
                "level too large: more than GATSPI_NOALLOC_MAX_ITEMS (gate, window) items; "
                "use fewer windows per call");
   const long long tiles = level_tiles(a->gate_end - a->gate_begin, a->num_windows, kNoAllocItemsPerThread);
+  const bool wide = wide_tiling(a->num_windows, kNoAllocItemsPerThread);
+  if (wide && ((uintptr_t)a->tile_info & 7u))
+    return say(a, GATSPI_EINVAL, "tile_info must be 8-byte aligned");
+  if (wide ? !a->tile_info : !a->rstart)
+    return say(a, GATSPI_EINVAL, wide ? "tile_info is null (needed with 64 or more windows)"
+                                      : "rstart is null (needed with fewer than 64 windows)");
   int device = 0;
   if (cudaGetDevice(&device) != cudaSuccess) return say(a, GATSPI_ECUDA, "cudaGetDevice failed");
   unsigned long long* scratch = nullptr;
@@ -102,7 +108,10 @@ extern "C" int gatspi_propagate_level_noalloc(const gatspi_level_args* a, void* 
   j.fanin_ptr = a->fanin_ptr; j.fanin_net = a->fanin_net; j.lut = a->lut;
   j.gate_delay = a->gate_delay; j.wire_delay = a->wire_delay; j.net_level = a->net_level;
   j.gate_delta = nullptr;
-  j.rstart = a->rstart; j.rmeta = a->rmeta; j.times = a->times; j.lvl_base = (long long*)a->lvl_base;
+  j.rstart = wide ? nullptr : a->rstart;
+  j.tinfo = wide ? (int2*)a->tile_info : nullptr;
+  j.T = wide ? (a->num_windows + tile_items_of(kNoAllocItemsPerThread) - 1) / tile_items_of(kNoAllocItemsPerThread) : 0;
+  j.rmeta = a->rmeta; j.times = a->times; j.lvl_base = (long long*)a->lvl_base;
   j.capacity = a->capacity;
   j.saif_t1 = (unsigned long long*)a->saif_t1; j.saif_tc = (unsigned long long*)a->saif_tc;
   j.status = a->status;
@@ -113,7 +122,6 @@ extern "C" int gatspi_propagate_level_noalloc(const gatspi_level_args* a, void* 
   p.seg.gate_begin = a->gate_begin;
   p.seg.n_items = (int32_t)items;
   p.seg.n_tiles = (int32_t)tiles;
-  p.seg.wide = wide_tiling(a->num_windows, kNoAllocItemsPerThread) ? 1 : 0;
   p.tile_counter = (int32_t*)(scratch + 1);
   SingleLaunch go{&p, s};
   go.go<kNoAllocThreads, kNoAllocItemsPerThread>();

@@ -196,7 +196,7 @@ def test_small_arena_retries_then_matches():
     is reported as ECAPACITY."""
     wl = gen.make_workload("tiny", seed=8, num_cycles=200)
     ref = oracle.EventSim(wl.netlist, wl.delays, wl.stim, W=1)
-    with gs.Simulator(wl.netlist, wl.delays, wl.stim, arena_bytes=3 << 20) as sim:
+    with gs.Simulator(wl.netlist, wl.delays, wl.stim, arena_bytes=1 << 20) as sim:
         sim.simulate()
         assert sim.stats()["batches"] > 1
         assert_saif_equal(sim, ref)

@@ -5,7 +5,8 @@ owned by a framework or a pool, no implicit device synchronization allowed,
 everything reserved up front) pass their own buffers to
 gatspi_propagate_level_noalloc.  This test plays such a caller: it lays out
 the waveform store the way the header describes, fills level 0 from the
-stimulus on the host, runs every level through the new entry point -- twice
+stimulus on the host (gate-aligned tiles: record metas plus tile runs),
+runs every level through the new entry point -- twice
 in a row, since calls share the library's fixed scratch -- and checks each
 run against gatspi_simulate bit for bit (SAIF of every gate net and the
 waveforms of sampled windows).  Kept in a file of its own, collected last.
@@ -29,22 +30,29 @@ def _levels(nl):
     return lv
 
 
+TW = 128  # windows per gate-aligned tile of the allocation-free entry point
+
+
 def _level0(wl, NW):
-    """Input records for windows 0..NW-1 (one cycle per window): start,
-    meta (start value in bit 15, edge count below) and the edge times."""
+    """Input records for windows 0..NW-1 (one cycle per window): meta
+    (start value in bit 15, edge count below), the tile runs (first edge,
+    edges) of every input's 128-window tiles, and the edge times."""
     st, I = wl.stim, wl.netlist.num_inputs
     C = st.num_cycles
-    start = np.zeros(I * NW, np.int32)
+    T = -(-NW // TW)
     meta = np.zeros(I * NW, np.uint16)
+    tinfo = np.zeros((I * T, 2), np.int32)
     times = []
     for i in range(I):
         for w in range(NW):
             a, b = int(st.edge_ptr[i * C + w]), int(st.edge_ptr[i * C + w + 1])
             v0 = int(st.init[i]) ^ ((a - int(st.edge_ptr[i * C])) & 1)
-            start[i * NW + w] = len(times)
             meta[i * NW + w] = (v0 << 15) | (b - a)
+            if w % TW == 0:
+                tinfo[i * T + w // TW, 0] = len(times)
+            tinfo[i * T + w // TW, 1] += b - a
             times += st.edge_time[a:b].tolist()
-    return start, meta, np.asarray(times, np.int32)
+    return meta, tinfo, np.asarray(times, np.int32)
 
 
 def test_noalloc_levels_match_simulate_twice():
@@ -74,9 +82,11 @@ def test_noalloc_levels_match_simulate_twice():
     gate_delay = t(wl.delays.gate_delay, torch.int32)
     wire_delay = t(wl.delays.wire_delay, torch.int32)
     net_level = t(lv, torch.int32)
-    start0, meta0, times0 = _level0(wl, NW)
+    assert NW >= 64                                 # gate-aligned tiles: tile runs, no rstart
+    T = -(-NW // TW)
+    meta0, tinfo0, times0 = _level0(wl, NW)
     capacity = 8 * N * NW + times0.size
-    rstart = torch.zeros(N * NW, dtype=torch.int32, device=dev)
+    tinfo = torch.zeros((N * T, 2), dtype=torch.int32, device=dev)
     rmeta = torch.zeros(N * NW, dtype=torch.int16, device=dev)
     times = torch.zeros(capacity, dtype=torch.int32, device=dev)
     lvl_base = torch.zeros(D + 2, dtype=torch.int64, device=dev)
@@ -86,7 +96,7 @@ def test_noalloc_levels_match_simulate_twice():
     err = ctypes.create_string_buffer(256)
 
     for run in range(2):
-        rstart[:I * NW] = t(start0, torch.int32)
+        tinfo[:I * T] = t(tinfo0, torch.int32)
         rmeta[:I * NW] = t(meta0.view(np.int16), torch.int16)
         times[:times0.size] = t(times0, torch.int32)
         lvl_base.zero_()
@@ -98,7 +108,7 @@ def test_noalloc_levels_match_simulate_twice():
         for level in range(1, D + 1):
             a = gs.gatspi_level_args(
                 fanin_ptr.data_ptr(), fanin_net.data_ptr(), lut.data_ptr(), gate_delay.data_ptr(),
-                wire_delay.data_ptr(), net_level.data_ptr(), rstart.data_ptr(), rmeta.data_ptr(),
+                wire_delay.data_ptr(), net_level.data_ptr(), None, tinfo.data_ptr(), rmeta.data_ptr(),
                 times.data_ptr(), lvl_base.data_ptr(), capacity, saif_t1.data_ptr(),
                 saif_tc.data_ptr(), status.data_ptr(), I, level, gate_begin[level],
                 gate_begin[level + 1], NW, 0, 1, C, wl.stim.cycle_ps, 256, ctypes.cast(err, ctypes.c_char_p))
@@ -113,13 +123,15 @@ def test_noalloc_levels_match_simulate_twice():
         assert np.array_equal(tc[I:], ref_tc[I:]), f"run {run}: TC differs"
         assert np.array_equal(C * wl.stim.cycle_ps - t1[I:], ref_t0[I:])
 
-        h_start = rstart.cpu().numpy()
+        h_tinfo = tinfo.cpu().numpy()
         h_meta = rmeta.cpu().numpy().view(np.uint16)
         h_times, h_base = times.cpu().numpy(), lvl_base.cpu().numpy()
         for w, (ri, rp, rt) in ref_windows.items():
             for n in range(I, N):
                 r = n * NW + w
-                s, c = int(h_start[r]), int(h_meta[r]) & 0x7FFF
+                t0 = w // TW * TW                   # the window's tile: run start + earlier counts
+                s = int(h_tinfo[n * T + w // TW, 0]) + int((h_meta[n * NW + t0:r] & 0x7FFF).sum())
+                c = int(h_meta[r]) & 0x7FFF
                 b0 = int(h_base[lv[n]])
                 got = h_times[b0 + s:b0 + s + c].tolist()
                 assert int(h_meta[r]) >> 15 == int(ri[n]), f"run {run} window {w} net {n}: start value"
@@ -132,7 +144,7 @@ def test_noalloc_rejects_levels_beyond_its_limit():
     err = ctypes.create_string_buffer(256)
     dummy = 16  # never dereferenced: the size check comes first
     # 4096 gates x 2^20 windows = 2^32 items, beyond GATSPI_NOALLOC_MAX_ITEMS
-    a = gs.gatspi_level_args(*([dummy] * 10), 1 << 20, dummy, dummy, dummy, 4, 1, 0, 4096,
+    a = gs.gatspi_level_args(*([dummy] * 11), 1 << 20, dummy, dummy, dummy, 4, 1, 0, 4096,
                              1 << 20, 0, 1, 1 << 20, 1000, 256,
                              ctypes.cast(err, ctypes.c_char_p))
     rc = gs.lib().gatspi_propagate_level_noalloc(ctypes.byref(a), None)
