@@ -521,6 +521,62 @@ __device__ __forceinline__ void linear_tile(const JobView& J, const SegView& S, 
                    });
 }
 
+// Exclusive prefix sums, in window order, of one pin's per-window edge
+// counts (bits 0-14 of m[k] for window k*32 + lane), written to out[] for
+// the n windows.  While the pin's run has fewer than 65536 edges, four
+// chunks of 32 windows share one 64-bit shuffle scan, 16 bits per chunk
+// (no field can carry into the next); longer runs scan chunk by chunk.
+template <int IPT>
+__device__ __forceinline__ void run_starts(const uint32_t (&m)[IPT], int lane, int32_t n, int32_t run_edges,
+                                           int32_t* out) {
+  if (run_edges < 65536) {
+    constexpr int NV = (IPT + 3) / 4;
+    unsigned long long v[NV], incl[NV];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+      v[q] = 0;
+#pragma unroll
+      for (int k = 4 * q; k < IPT && k < 4 * q + 4; ++k)
+        v[q] |= (unsigned long long)(m[k] & (uint32_t)kMaxCount) << (16 * (k - 4 * q));
+      incl[q] = v[q];
+    }
+#pragma unroll
+    for (int dd = 1; dd < 32; dd <<= 1) {
+#pragma unroll
+      for (int q = 0; q < NV; ++q) {
+        const unsigned long long u = __shfl_up_sync(0xffffffffu, incl[q], dd);
+        if (lane >= dd) incl[q] += u;
+      }
+    }
+    int32_t carry = 0;
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+      const unsigned long long tot = __shfl_sync(0xffffffffu, incl[q], 31);
+      const unsigned long long ex = incl[q] - v[q];
+#pragma unroll
+      for (int k = 4 * q; k < IPT && k < 4 * q + 4; ++k) {
+        const int sh = 16 * (k - 4 * q);
+        if (k * 32 + lane < n) out[k * 32 + lane] = carry + (int32_t)((ex >> sh) & 0xffffull);
+        carry += (int32_t)((tot >> sh) & 0xffffull);
+      }
+    }
+  } else {
+    int32_t carry = 0;
+#pragma unroll
+    for (int k = 0; k < IPT; ++k) {
+      const int32_t c = (int32_t)(m[k] & (uint32_t)kMaxCount);
+      int32_t incl = c;
+#pragma unroll
+      for (int dd = 1; dd < 32; dd <<= 1) {
+        const int32_t u = __shfl_up_sync(0xffffffffu, incl, dd);
+        if (lane >= dd) incl += u;
+      }
+      if (k * 32 + lane < n) out[k * 32 + lane] = carry + incl - c;
+      carry += __shfl_sync(0xffffffffu, incl, 31);
+    }
+  }
+}
+
 // A gate's fanin nets and their levels, first pin, truth table and pin
 // count: one 32-byte descriptor, or the CSR arrays when there is none.
 struct GateDesc {
@@ -627,21 +683,7 @@ __device__ __forceinline__ void wide_tile_k(const JobView& J, const SegView& S, 
     for (int k = 0; k < IPT; ++k)
       if (k * 32 + lane < n) sm.smeta[i][k * 32 + lane] = (uint16_t)mv[i][k];
     // edge starts inside the run: exclusive scan of the counts in window order
-    if (lim[i] > 0) {
-      int32_t carry = 0;
-#pragma unroll
-      for (int k = 0; k < IPT; ++k) {
-        const int32_t c = (int32_t)(mv[i][k] & (uint32_t)kMaxCount);
-        int32_t incl = c;
-#pragma unroll
-        for (int dd = 1; dd < 32; dd <<= 1) {
-          const int32_t v = __shfl_up_sync(0xffffffffu, incl, dd);
-          if (lane >= dd) incl += v;
-        }
-        if (k * 32 + lane < n) sm.sstart[i][k * 32 + lane] = carry + incl - c;
-        carry += __shfl_sync(0xffffffffu, incl, 31);
-      }
-    }
+    if (lim[i] > 0) run_starts<IPT>(mv[i], lane, n, lim[i], sm.sstart[i]);
   }
 
   // 2. settle quiet windows, list the others (window order: k-major, lane-minor)
