@@ -51,6 +51,28 @@ def _peaks():
         return 6800.0, "fallback"
 
 
+def _traffic(tile_threads, items_per_thread):
+    """DRAM bytes per propagation launch from the committed ncu summary, or
+    None once the kernel source or the launch shape differs from the one the
+    counters were taken on."""
+    import hashlib
+    try:
+        fields = {}
+        with open(os.path.join(ROOT, "profiles", "propagate_kernel_traffic.txt")) as f:
+            for line in f:
+                if ":" in line and not line.startswith("#"):
+                    k, v = line.split(":", 1)
+                    fields[k.strip()] = v.strip()
+        with open(os.path.join(ROOT, "paper_2203_06117_gb300", "csrc", "kernels.cuh"), "rb") as f:
+            digest = hashlib.sha256(f.read()).hexdigest()
+        if (fields.get("kernels_cuh_sha256") != digest or int(fields["tile_threads"]) != tile_threads
+                or int(fields["items_per_thread"]) != items_per_thread):
+            return None
+        return int(fields["traffic_bytes_per_launch"])
+    except (OSError, KeyError, ValueError):
+        return None
+
+
 # ----------------------------------------------------------- CPU oracle leg
 
 _WORKER = {}
@@ -406,7 +428,10 @@ def main():
         "e2e": {"value": units * world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h)},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
+                     "frac": achieved / peak,
+                     "traffic": _traffic(st["tile_threads"], st["items_per_thread"])
+                     if WORKLOAD == "mid" and not args.cycles else None,
+                     "peak_kind": peak_kind,
                      "kernel": "propagate_kernel",
                      "algo_bytes_per_step": int(algo[-1]), "prop_ms_per_step": statistics.mean(prop_ms),
                      "launches_per_step": prop_launches // args.steps},

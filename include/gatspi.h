@@ -92,9 +92,14 @@ typedef struct gatspi_stats {
   int64_t items;           /* (gate, window) items simulated */
   int64_t edges;           /* waveform edges stored, all nets and windows */
   int64_t algo_bytes;      /* algorithmic bytes of the propagation kernels:
-                              per (gate, window) item, per fanin pin
-                              4 (offset) + 1 (start value) + 4 * edges read,
-                              plus 4 + 1 + 4 * edges written for the output */
+                              per (gate, window) item and fanin pin a 2-byte
+                              record read, per item a 2-byte record written;
+                              per (pin or gate, tile of 32 * items_per_thread
+                              windows) an 8-byte tile run read or written
+                              (with at least 16 * items_per_thread windows
+                              per batch; else a 4-byte start per record);
+                              4 bytes per edge read by each fanin pin and per
+                              edge written */
   int32_t batches;         /* device batches of windows */
   int32_t windows;         /* windows simulated */
   int32_t batch_windows;   /* windows per batch actually used */

@@ -412,7 +412,7 @@ int simulate_impl(gatspi_ctx* ctx, const gatspi_opts* opts) {
   while (NW > 1 && fixed_bytes(ctx, NW, ipt) * 2 > ctx->arena_limit) NW = (NW + 1) / 2;
 
   int32_t w0 = 0;
-  int64_t edges_total = 0;
+  int64_t edges_total = 0, rec_bytes = 0;
   while (w0 < n_windows) {
     const int32_t nw = std::min(NW, n_windows - w0);
     int rc = ensure_arena(ctx, want_bytes(nw));
@@ -510,6 +510,7 @@ int simulate_impl(gatspi_ctx* ctx, const gatspi_opts* opts) {
       // if we restart from w0 = 0
       w0 = 0;
       edges_total = 0;
+      rec_bytes = 0;
       first_recorded = false;
       st = gatspi_stats{};
       st.levels = ctx->D;
@@ -529,6 +530,12 @@ int simulate_impl(gatspi_ctx* ctx, const gatspi_opts* opts) {
       }
     }
     edges_total += lvl_end;
+    // record bytes of the batch: a 2-byte meta per record read by every pin
+    // and written per gate, plus an 8-byte tile run per (pin or gate, tile)
+    // with gate-aligned tiles, or a 4-byte start per record without
+    rec_bytes += ctx->batch_T > 0
+                     ? ((int64_t)ctx->P + ctx->G) * (2ll * nw + 8ll * ctx->batch_T)
+                     : ((int64_t)ctx->P + ctx->G) * 6ll * nw;
     ctx->batch_w0 = w0;
     ctx->batch_nw = nw;
     st.batches++;
@@ -538,12 +545,13 @@ int simulate_impl(gatspi_ctx* ctx, const gatspi_opts* opts) {
   st.batch_windows = NW;
   st.edges = edges_total;
   ctx->total_time = (int64_t)ctx->C * ctx->L;
-  // algorithmic bytes: per item and pin 4 + 1 + 4 * edges read, per item
-  // 4 + 1 + 4 * edges written; edges read by a pin = TC of its driving net
+  // algorithmic bytes: the records' bytes above, plus 4 bytes per edge read
+  // by every fanin pin (a pin reads the TC of its driving net) and per edge
+  // written by a gate
   {
     std::vector<unsigned long long> tc(ctx->N);
     CK(cudaMemcpy(tc.data(), ctx->d_tc, sizeof(unsigned long long) * ctx->N, cudaMemcpyDeviceToHost));
-    int64_t b = 5ll * ((int64_t)ctx->P + ctx->G) * n_windows;
+    int64_t b = rec_bytes;
     for (int32_t n = 0; n < ctx->N; ++n)
       b += 4ll * (int64_t)tc[n] * (ctx->fanout[n] + (n >= ctx->I ? 1 : 0));
     st.algo_bytes = b;
@@ -558,13 +566,14 @@ int simulate_impl(gatspi_ctx* ctx, const gatspi_opts* opts) {
 
 // Pick the launch shape (threads per block x consecutive windows per
 // thread) by timing every compiled variant on the first windows of the
-// loaded stimulus (about 10^8 (gate, window) items); cached per netlist.
+// loaded stimulus (about 4*10^8 (gate, window) items, the best of two
+// timed runs after a warm-up); cached per netlist.
 int autotune(gatspi_ctx* ctx, const gatspi_opts& base) {
   static const int kVariants[][2] = {{256, 1}, {256, 2}, {256, 4}, {256, 8}, {128, 4},
                                      {128, 8}, {512, 1}, {512, 2}, {512, 4}};
   const int32_t W = base.window_cycles ? base.window_cycles : 1;
   const int32_t n_windows = (ctx->C + W - 1) / W;
-  const int64_t want = (int64_t)1e8 / std::max<int64_t>(ctx->N, 1);
+  const int64_t want = (int64_t)4e8 / std::max<int64_t>(ctx->N, 1);
   ctx->window_limit = (int32_t)std::max<int64_t>(1, std::min<int64_t>(want, n_windows));
   double best = 1e300;
   int bn = 256, bi = 4, rc = GATSPI_OK;
@@ -573,10 +582,10 @@ int autotune(gatspi_ctx* ctx, const gatspi_opts& base) {
     o.tile_items = v[0];
     o.items_per_thread = v[1];
     o.time_kernels = 1;
-    double ms = 0;
-    for (int rep = 0; rep < 2 && rc == GATSPI_OK; ++rep) {
+    double ms = 1e300;
+    for (int rep = 0; rep < 3 && rc == GATSPI_OK; ++rep) {
       rc = simulate_impl(ctx, &o);
-      ms = ctx->stats.prop_ms;
+      if (rep > 0) ms = std::min(ms, ctx->stats.prop_ms);  // the first run warms up
     }
     if (rc != GATSPI_OK) break;
     if (ms < best) {
