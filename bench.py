@@ -275,15 +275,16 @@ def run_batched_mode(args):
     nets, specs = gen.batched_workload(seed=SEED, scale=args.scale)
     work = sum(nets[s["netlist"]].netlist.num_gates * s["stim"].num_cycles for s in specs)
     reqs = [serve.Request.from_spec(s) for s in specs]
-    opts = dict(tile_items=args.tile, items_per_thread=args.ipt)
-    serve.run_batched(nets, reqs, keep_results=False, **opts)          # warm-up
+    opts = dict(tile_items=args.tile or 256, items_per_thread=args.ipt or 4)
+    eopts = dict(opts, step_items=args.step_items)
+    serve.run_batched(nets, reqs, keep_results=False, **eopts)         # warm-up
     t_b = []
     for _ in range(args.steps):
-        dt, st = serve.run_batched(nets, reqs, **opts)
+        dt, st = serve.run_batched(nets, reqs, **eopts)
         t_b.append(dt)
     batched = [r.result for r in reqs]
-    serve.run_plain_loop(nets, reqs, keep_results=False)               # warm-up
-    t_p = [serve.run_plain_loop(nets, reqs) for _ in range(args.steps)]
+    serve.run_plain_loop(nets, reqs, keep_results=False, **opts)       # warm-up
+    t_p = [serve.run_plain_loop(nets, reqs, **opts) for _ in range(args.steps)]
     exact = all(_saif_equal(a, r.result) for a, r in zip(batched, reqs))
     tb, tp = statistics.median(t_b), statistics.median(t_p)
     line = {"metric": "batched gate*cycle evals/s", "value": work / tb, "unit": UNIT, "n_gpus": 1,
@@ -309,13 +310,16 @@ def run_served_mode(args):
     work = sum(nets[s["netlist"]].netlist.num_gates * s["stim"].num_cycles for s in specs)
     # warm-up on a short prefix of the stream
     warm = [serve.Request.from_spec(s) for s in specs[:8]]
-    serve.run_served(nets, warm, keep_results=False, tile_items=args.tile, items_per_thread=args.ipt)
+    opts = dict(tile_items=args.tile or 256, items_per_thread=args.ipt or 4)
+    eopts = dict(opts, step_items=args.step_items)
+    serve.run_served(nets, warm, keep_results=False, **eopts)
     reqs = [serve.Request.from_spec(s) for s in specs]
-    mk, st = serve.run_served(nets, reqs, tile_items=args.tile, items_per_thread=args.ipt)
+    mk, st = serve.run_served(nets, reqs, **eopts)
     served = [r.result for r in reqs]
     lat = serve.latency_summary(reqs)
     reqs_p = [serve.Request.from_spec(s) for s in specs]
-    mk_p = serve.run_served_plain(nets, reqs_p)
+    serve.run_served_plain(nets, warm, keep_results=False, **opts)
+    mk_p = serve.run_served_plain(nets, reqs_p, **opts)
     lat_p = serve.latency_summary(reqs_p)
     exact = all(_saif_equal(a, r.result) for a, r in zip(served, reqs_p))
     line = {"metric": "served gate*cycle evals/s", "value": work / mk, "unit": UNIT, "n_gpus": 1,
@@ -351,6 +355,8 @@ def main():
                          "multi-job engine against the plain per-job path")
     ap.add_argument("--scale", type=float, default=1.0, help="shrink batched/served workloads")
     ap.add_argument("--rate", type=float, default=200.0)
+    ap.add_argument("--step-items", type=int, default=0,
+                    help="engine: (gate, window) items per step to admit up to (0: the engine's default)")
     ap.add_argument("--seconds", type=float, default=1.0)
     args = ap.parse_args()
     if args.workload == "batched":

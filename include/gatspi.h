@@ -227,10 +227,15 @@ typedef struct gatspi_engine_opts {
   int32_t tile_items;  /* threads per block for every launch: 128, 256, 512;
                           0 = 256 */
   int32_t max_active;  /* parts in flight at once; 0 = 1024 */
-  int64_t part_items;  /* max (gate, window) items of one part; 0 = 2^28 */
+  int64_t part_items;  /* max (gate, window) items of one part; 0 = 2^30 */
   int32_t items_per_thread; /* 1, 2, 4, 8 (at most 4 with 512 threads);
                                0 = 4 */
-  int32_t reserved[3]; /* must be 0 */
+  int32_t reserved;    /* must be 0 */
+  int64_t step_items;  /* admission stops while the parts in flight hold
+                          this many (gate, window) items per level on
+                          average: enough to fill the GPU in one launch,
+                          few enough that a step's levels stay in L2;
+                          0 = 2^25 */
 } gatspi_engine_opts;
 
 typedef struct gatspi_engine_stats {
@@ -242,6 +247,8 @@ typedef struct gatspi_engine_stats {
   int64_t bytes_peak;     /* largest device bytes held by admitted parts */
   int32_t active;         /* parts in flight now */
   int32_t queued;         /* parts waiting for admission now */
+  double host_ms;         /* host time spent inside gatspi_engine_step */
+  double wait_ms;         /* of which blocked waiting for the device */
 } gatspi_engine_stats;
 
 /* Job states reported by gatspi_engine_poll. */

@@ -87,14 +87,15 @@ class gatspi_opts(ctypes.Structure):
 class gatspi_engine_opts(ctypes.Structure):
     _fields_ = [("tile_items", ctypes.c_int32), ("max_active", ctypes.c_int32),
                 ("part_items", ctypes.c_int64), ("items_per_thread", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 3)]
+                ("reserved", ctypes.c_int32), ("step_items", ctypes.c_int64)]
 
 
 class gatspi_engine_stats(ctypes.Structure):
     _fields_ = [("steps", ctypes.c_int64), ("kernel_launches", ctypes.c_int64),
                 ("parts_done", ctypes.c_int64), ("parts_retried", ctypes.c_int64),
                 ("items", ctypes.c_int64), ("bytes_peak", ctypes.c_int64),
-                ("active", ctypes.c_int32), ("queued", ctypes.c_int32)]
+                ("active", ctypes.c_int32), ("queued", ctypes.c_int32),
+                ("host_ms", ctypes.c_double), ("wait_ms", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -312,9 +313,10 @@ def _echeck(eng, rc):
 
 
 def gatspi_engine_create(device=0, arena_bytes=0, tile_items=0, max_active=0, part_items=0,
-                         items_per_thread=0):
+                         items_per_thread=0, step_items=0):
     h = ctypes.c_void_p()
-    o = gatspi_engine_opts(int(tile_items), int(max_active), int(part_items), int(items_per_thread))
+    o = gatspi_engine_opts(int(tile_items), int(max_active), int(part_items), int(items_per_thread), 0,
+                           int(step_items))
     rc = lib().gatspi_engine_create(ctypes.byref(h), int(device), int(arena_bytes), ctypes.byref(o))
     if rc != OK:
         raise GatspiError(rc, f"cannot create an engine on device {device}")

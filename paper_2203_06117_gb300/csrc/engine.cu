@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cstring>
 #include <deque>
 #include <map>
@@ -64,6 +65,7 @@ struct EPart {
   int64_t job = 0;
   int32_t w0 = 0, nw = 0, level = 0, D = 0;
   int64_t edge_hint = 0;
+  int64_t level_items = 0;  // (gate, window) items of an average level
   char* mem = nullptr;
   size_t bytes = 0;
   int32_t* rstart = nullptr;  // linear tiling
@@ -89,6 +91,7 @@ struct gatspi_engine {
   cudaStream_t stream = nullptr;
   std::string err;
   size_t budget = 0, in_use = 0;
+  int64_t step_load = 0;  // average level items of the parts in flight
   gatspi_engine_opts opts{};
   int nt = 256, ipt = 4;
   int tile = 128;  // items per warp tile (linear tiling)
@@ -106,7 +109,7 @@ struct gatspi_engine {
   int ring = 0;
   char* d_stage = nullptr;
   size_t d_stage_cap = 0;
-  int32_t* d_counter = nullptr;
+  int32_t* d_counter = nullptr;  // one tile counter per launch of a step
   // pinned per-part result slots
   PartResult* h_results = nullptr;
   std::vector<int32_t> free_slots;
@@ -247,7 +250,9 @@ int retire(gatspi_engine* eng, bool wait_one) {
     EPart& p = *eng->finishing[k];
     cudaError_t q = cudaEventQuery(p.ev);
     if (q == cudaErrorNotReady && wait_one && !waited) {
+      const auto tw = std::chrono::steady_clock::now();
       ECK(cudaEventSynchronize(p.ev));
+      eng->stats.wait_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - tw).count();
       waited = true;
       q = cudaSuccess;
     }
@@ -324,8 +329,7 @@ int gatspi_engine_create(gatspi_engine** out, int device, size_t arena_bytes, co
   }
   gatspi_engine_opts o{};
   if (opts) o = *opts;
-  for (int k = 0; k < 3; ++k)
-    if (o.reserved[k]) return GATSPI_EINVAL;
+  if (o.reserved || o.step_items < 0) return GATSPI_EINVAL;
   const int nt = o.tile_items ? o.tile_items : 256;
   const int ipt = o.items_per_thread ? o.items_per_thread : 4;
   if ((nt != 128 && nt != 256 && nt != 512) || (ipt != 1 && ipt != 2 && ipt != 4 && ipt != 8) ||
@@ -339,10 +343,12 @@ int gatspi_engine_create(gatspi_engine** out, int device, size_t arena_bytes, co
   eng->ipt = ipt;
   eng->tile = tile_items_of(ipt);
   if (!eng->opts.max_active) eng->opts.max_active = 1024;
-  if (!eng->opts.part_items) eng->opts.part_items = 1ll << 28;
+  if (!eng->opts.part_items) eng->opts.part_items = 1ll << 30;
+  if (!eng->opts.step_items) eng->opts.step_items = 1ll << 25;
   if (cudaSetDevice(device) != cudaSuccess ||
       cudaStreamCreateWithFlags(&eng->stream, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaMalloc(&eng->d_counter, sizeof(int32_t)) != cudaSuccess ||
+      cudaMalloc(&eng->d_counter, sizeof(int32_t) * (size_t)(eng->opts.max_active / kMaxSegs + 2)) !=
+          cudaSuccess ||
       cudaMallocHost(&eng->h_results, sizeof(PartResult) * (size_t)eng->opts.max_active) != cudaSuccess) {
     cudaGetLastError();
     gatspi_engine_destroy(eng);
@@ -496,7 +502,7 @@ int gatspi_engine_submit(gatspi_engine* eng, int32_t netlist_id, int32_t num_cyc
   return GATSPI_OK;
 }
 
-int gatspi_engine_step(gatspi_engine* eng, int32_t* active_out, int32_t* queued_out) {
+static int engine_step_impl(gatspi_engine* eng, int32_t* active_out, int32_t* queued_out) {
   if (!eng) return GATSPI_EINVAL;
   ECK(cudaSetDevice(eng->device));
   // 1. retire (block on the oldest finishing part only if nothing else can move)
@@ -508,7 +514,8 @@ int gatspi_engine_step(gatspi_engine* eng, int32_t* active_out, int32_t* queued_
   std::vector<EPart*> admitted;
   std::vector<std::vector<long long>> prefixes;
   while (!eng->queued.empty() &&
-         (int32_t)(eng->active.size() + eng->finishing.size()) < eng->opts.max_active) {
+         (int32_t)(eng->active.size() + eng->finishing.size()) < eng->opts.max_active &&
+         (eng->active.empty() || eng->step_load < eng->opts.step_items)) {
     EPart& p = *eng->queued.front();
     EJob& j = *eng->jobs.at(p.job);
     if (j.state == GATSPI_JOB_FAILED) {
@@ -550,6 +557,8 @@ int gatspi_engine_step(gatspi_engine* eng, int32_t* active_out, int32_t* queued_
     own->bytes = bytes;
     part_layout(nl, *own, eng->ipt, own->mem);
     eng->in_use += bytes;
+    own->level_items = (int64_t)own->nw * nl.r.G / std::max<int32_t>(nl.r.D, 1);
+    eng->step_load += own->level_items;
     eng->stats.bytes_peak = std::max<int64_t>(eng->stats.bytes_peak, (int64_t)eng->in_use);
     ECK(cudaMemsetAsync(own->mem + own->zero_off, 0, own->zero_bytes, eng->stream));
     std::vector<long long> pre(nl.r.I);
@@ -576,20 +585,19 @@ int gatspi_engine_step(gatspi_engine* eng, int32_t* active_out, int32_t* queued_
   for (auto& p : eng->active)
     if (p->level >= 1 || std::find(admitted.begin(), admitted.end(), p.get()) != admitted.end())
       stepping.push_back(p.get());
-  const size_t jobs_off = bytes;
-  bytes = (size_t)align_up((int64_t)(bytes + stepping.size() * sizeof(JobView)));
-  const size_t segs_off = bytes;
-  bytes = (size_t)align_up((int64_t)(bytes + stepping.size() * sizeof(MultiSeg)));
   if ((rc = stage_reserve(eng, std::max<size_t>(bytes, 4096)))) return rc;
   const int slot = eng->ring;
   eng->ring = (eng->ring + 1) % gatspi_engine::kRing;
-  ECK(cudaEventSynchronize(eng->stage_ev[slot]));
+  {
+    const auto tw = std::chrono::steady_clock::now();
+    ECK(cudaEventSynchronize(eng->stage_ev[slot]));
+    eng->stats.wait_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - tw).count();
+  }
   char* h = eng->h_stage[slot];
   for (size_t k = 0; k < admitted.size(); ++k)
     std::memcpy(h + pre_off[k], prefixes[k].data(), prefixes[k].size() * sizeof(long long));
   // levels: admitted parts run level 0 (inputs kernel) in this step and
   // level 1 onwards from the next step
-  std::vector<JobView> views;
   std::vector<MultiSeg> segs;
   int64_t tiles = 0;
   for (EPart* p : stepping) {
@@ -603,34 +611,39 @@ int gatspi_engine_step(gatspi_engine* eng, int32_t* active_out, int32_t* queued_
     s.seg.gate_begin = nl.r.lvl_gate_begin[l];
     s.seg.n_items = (nl.r.lvl_gate_begin[l + 1] - nl.r.lvl_gate_begin[l]) * p->nw;
     s.seg.n_tiles = (int32_t)level_tiles(nl.r.lvl_gate_begin[l + 1] - nl.r.lvl_gate_begin[l], p->nw, eng->ipt);
-    s.job = (int32_t)views.size();
-    s.tile_begin = (int32_t)tiles;
+    s.job = make_view(nl, j, *p);
+    s.tile_begin = 0;
     tiles += s.seg.n_tiles;
-    views.push_back(make_view(nl, j, *p));
     segs.push_back(s);
     eng->stats.items += s.seg.n_items;
   }
-  if (tiles > 0x7fffff00ll) return efail(eng, GATSPI_ECAPACITY, "too many tiles in one step");
-  std::memcpy(h + jobs_off, views.data(), views.size() * sizeof(JobView));
-  std::memcpy(h + segs_off, segs.data(), segs.size() * sizeof(MultiSeg));
   if (bytes) ECK(cudaMemcpyAsync(eng->d_stage, h, bytes, cudaMemcpyHostToDevice, eng->stream));
   ECK(cudaEventRecord(eng->stage_ev[slot], eng->stream));
 
   // 4. launches: the propagation step for parts already past level 0, then
   // level 0 of the admitted parts
   if (tiles > 0) {
-    ECK(cudaMemsetAsync(eng->d_counter, 0, sizeof(int32_t), eng->stream));
-    MultiParams m{};
-    m.jobs = (const JobView*)(eng->d_stage + jobs_off);
-    m.segs = (const MultiSeg*)(eng->d_stage + segs_off);
-    m.n_segs = (int32_t)segs.size();
-    m.n_tiles = (int32_t)tiles;
-    m.tile_counter = eng->d_counter;
-    MultiLaunch go{&m, eng->stream};
-    launch_variant(eng->nt, eng->ipt, go);
-    ECK(cudaGetLastError());
+    // one launch per kMaxSegs segments, each with its own tile counter
+    const size_t n_launch = (segs.size() + kMaxSegs - 1) / kMaxSegs;
+    ECK(cudaMemsetAsync(eng->d_counter, 0, sizeof(int32_t) * n_launch, eng->stream));
+    for (size_t c = 0; c < n_launch; ++c) {
+      MultiParams m{};
+      int64_t t = 0;
+      for (size_t k = c * kMaxSegs; k < segs.size() && k < (c + 1) * kMaxSegs; ++k) {
+        MultiSeg& s = m.segs[m.n_segs++];
+        s = segs[k];
+        s.tile_begin = (int32_t)t;
+        t += s.seg.n_tiles;
+      }
+      if (t > 0x7fffff00ll) return efail(eng, GATSPI_ECAPACITY, "too many tiles in one launch");
+      m.n_tiles = (int32_t)t;
+      m.tile_counter = eng->d_counter + c;
+      MultiLaunch go{&m, eng->stream};
+      launch_variant(eng->nt, eng->ipt, go);
+      ECK(cudaGetLastError());
+      eng->stats.kernel_launches++;
+    }
     eng->stats.steps++;
-    eng->stats.kernel_launches++;
   }
   for (size_t k = 0; k < admitted.size(); ++k) {
     EPart& p = *admitted[k];
@@ -675,6 +688,7 @@ int gatspi_engine_step(gatspi_engine* eng, int32_t* active_out, int32_t* queued_
       ECK(cudaMemcpyAsync(&r->edges, p.lvl_base + p.D + 1, sizeof(long long), cudaMemcpyDeviceToHost,
                           eng->stream));
       ECK(cudaEventRecord(p.ev, eng->stream));
+      eng->step_load -= p.level_items;
       eng->finishing.push_back(std::move(eng->active[k]));
       eng->active.erase(eng->active.begin() + (long)k);
       continue;
@@ -693,6 +707,14 @@ int gatspi_engine_step(gatspi_engine* eng, int32_t* active_out, int32_t* queued_
   if (active_out) *active_out = eng->stats.active;
   if (queued_out) *queued_out = eng->stats.queued;
   return GATSPI_OK;
+}
+
+int gatspi_engine_step(gatspi_engine* eng, int32_t* active_out, int32_t* queued_out) {
+  if (!eng) return GATSPI_EINVAL;
+  const auto t = std::chrono::steady_clock::now();
+  const int rc = engine_step_impl(eng, active_out, queued_out);
+  eng->stats.host_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t).count();
+  return rc;
 }
 
 int gatspi_engine_drain(gatspi_engine* eng) {

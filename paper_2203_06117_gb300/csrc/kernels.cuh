@@ -99,18 +99,22 @@ struct PropParams {
 };
 
 struct MultiSeg {
+  JobView job;
   SegView seg;
-  int32_t job;         // index into the job table
   int32_t tile_begin;  // first launch-wide tile of this segment
 };
 
+// Segments of one multi-job launch.  The table travels in the kernel's
+// parameter space (read through the constant cache), so finding a tile's
+// job costs no global-memory round trip.
+constexpr int kMaxSegs = 32;
 struct MultiParams {
-  const JobView* jobs;
-  const MultiSeg* segs;  // sorted by tile_begin
   int32_t n_segs;
   int32_t n_tiles;        // tiles of all segments
   int32_t* tile_counter;  // zero before the launch
+  MultiSeg segs[kMaxSegs];  // sorted by tile_begin
 };
+static_assert(sizeof(MultiParams) < 32000, "kernel parameters are limited to 32 KB");
 
 __device__ __forceinline__ int32_t window_len(int32_t wg, int32_t W, int32_t C, int32_t L) {
   const int32_t c0 = wg * W;
@@ -898,27 +902,18 @@ template <int NT, int IPT>
 __global__ void __launch_bounds__(NT, (min_blocks<NT, IPT>())) propagate_multi_kernel(const __grid_constant__ MultiParams m) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   WarpSmem<IPT>* sm = reinterpret_cast<WarpSmem<IPT>*>(smem_raw);
-  __shared__ JobView s_job[NT / 32];
-  __shared__ SegView s_seg[NT / 32];
   __shared__ int32_t s_first;
-  const int warp = threadIdx.x >> 5;
   if (threadIdx.x == 0) s_first = atomicAdd(m.tile_counter, NT / 32);
   __syncthreads();
-  int32_t t = s_first + warp;
+  const int32_t t = s_first + (int32_t)(threadIdx.x >> 5);
   if (t >= m.n_tiles) return;
-  if ((threadIdx.x & 31) == 0) {
-    int32_t lo = 0, hi = m.n_segs - 1;
-    while (lo < hi) {  // last segment with tile_begin <= t
-      const int32_t mid = (lo + hi + 1) >> 1;
-      if (m.segs[mid].tile_begin <= t) lo = mid; else hi = mid - 1;
-    }
-    s_seg[warp] = m.segs[lo].seg;
-    s_job[warp] = m.jobs[m.segs[lo].job];
-    t -= m.segs[lo].tile_begin;
+  int32_t lo = 0, hi = m.n_segs - 1;
+  while (lo < hi) {  // last segment with tile_begin <= t
+    const int32_t mid = (lo + hi + 1) >> 1;
+    if (m.segs[mid].tile_begin <= t) lo = mid; else hi = mid - 1;
   }
-  t = __shfl_sync(0xffffffffu, t, 0);
-  __syncwarp();
-  propagate_warp<IPT>(s_job[warp], s_seg[warp], t, sm[warp]);
+  const MultiSeg& sg = m.segs[lo];
+  propagate_warp<IPT>(sg.job, sg.seg, t - sg.tile_begin, sm[threadIdx.x >> 5]);
 }
 
 // Items per tile (one warp's tile) for a variant.

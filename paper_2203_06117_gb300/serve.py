@@ -71,8 +71,10 @@ def run_batched(netlists, reqs, keep_results=True, **engine_opts):
         return dt, eng.stats()
 
 
-def run_plain_loop(netlists, reqs, keep_results=True):
-    """The single-job path, one job after the other (netlists resident)."""
+def run_plain_loop(netlists, reqs, keep_results=True, tile_items=256, items_per_thread=4):
+    """The single-job path, one job after the other (netlists resident), with
+    the engine's default launch shape (no per-netlist autotuning inside the
+    timed loop)."""
     sims = [Simulator(w.netlist, w.delays, _dummy_stim(w)) for w in netlists]
     try:
         t0 = time.perf_counter()
@@ -81,7 +83,8 @@ def run_plain_loop(netlists, reqs, keep_results=True):
             gatspi_set_edit(ctx, r.edit_gate, r.edit_delta)
             gatspi_set_stimulus(ctx, r.stim.num_cycles, r.stim.cycle_ps, r.stim.init, r.stim.edge_ptr,
                                 r.stim.edge_time)
-            gatspi_simulate(ctx, window_cycles=r.window_cycles)
+            gatspi_simulate(ctx, window_cycles=r.window_cycles, tile_items=tile_items,
+                            items_per_thread=items_per_thread)
             saif = sims[r.netlist].saif()
             r.result = saif if keep_results else None
             r.done = time.perf_counter() - t0
@@ -139,8 +142,9 @@ def run_served(netlists, reqs, keep_results=True, **engine_opts):
         return makespan, eng.stats()
 
 
-def run_served_plain(netlists, reqs, keep_results=True):
-    """The same stream, one request at a time on the single-job path."""
+def run_served_plain(netlists, reqs, keep_results=True, tile_items=256, items_per_thread=4):
+    """The same stream, one request at a time on the single-job path, with
+    the engine's default launch shape."""
     reqs = sorted(reqs, key=lambda r: r.arrival)
     sims = [Simulator(w.netlist, w.delays, _dummy_stim(w)) for w in netlists]
     try:
@@ -153,7 +157,8 @@ def run_served_plain(netlists, reqs, keep_results=True):
             gatspi_set_edit(ctx, r.edit_gate, r.edit_delta)
             gatspi_set_stimulus(ctx, r.stim.num_cycles, r.stim.cycle_ps, r.stim.init, r.stim.edge_ptr,
                                 r.stim.edge_time)
-            gatspi_simulate(ctx, window_cycles=r.window_cycles)
+            gatspi_simulate(ctx, window_cycles=r.window_cycles, tile_items=tile_items,
+                            items_per_thread=items_per_thread)
             saif = sims[r.netlist].saif()
             r.result = saif if keep_results else None
             r.done = time.perf_counter() - t0
