@@ -581,6 +581,14 @@ __device__ __forceinline__ void run_starts(const uint32_t (&m)[IPT], int lane, i
   }
 }
 
+// 4-byte asynchronous global-to-shared copy (cp.async, cached in L1), and
+// the wait for all of this thread's outstanding copies.
+__device__ __forceinline__ void cp_async4(int32_t* smem, const int32_t* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 // A gate's fanin nets and their levels, first pin, truth table and pin
 // count: one 32-byte descriptor, or the CSR arrays when there is none.
 struct GateDesc {
@@ -681,8 +689,10 @@ __device__ __forceinline__ void wide_tile_k(const JobView& J, const SegView& S, 
       if (!ok && lane == 0) atomicOr(J.status, kStCorrupt);
       lim[i] = ok ? c : 0;
       if (ok && used + c <= POOL) {
+        // asynchronous copies: the pins' runs are all in flight while the
+        // warp scans counts and settles quiet windows
         const int32_t* gsrc = J.times + base[i] + lo;
-        for (int j = lane; j < c; j += 32) sm.spool[used + j] = __ldg(gsrc + j);
+        for (int j = lane; j < c; j += 32) cp_async4(&sm.spool[used + j], gsrc + j);
         src[i] = &sm.spool[used];
         used += c;
       } else {
@@ -726,7 +736,8 @@ __device__ __forceinline__ void wide_tile_k(const JobView& J, const SegView& S, 
     }
     n_act += __popc(amask);
   }
-  __syncwarp();
+  cp_async_wait_all();  // the staged runs; the barrier then publishes every
+  __syncwarp();         // lane's copies, list entries and metas
 
   const int32_t* gd = &sm.sgd[0][0];
   auto pins_of = [&](int32_t wl, Pin (&pin)[K]) {
