@@ -59,6 +59,7 @@ struct gatspi_ctx {
   int64_t* d_edge_ptr = nullptr;
   int32_t* d_edge_time = nullptr;
   uint8_t* d_init_in = nullptr;
+  size_t cap_edge_ptr = 0, cap_edge_time = 0, cap_init_in = 0;  // elements the buffers hold
   std::vector<uint8_t> init_in;
 
   // SAIF and status
@@ -130,6 +131,20 @@ void free_netlist(gatspi_ctx* c) {
 
 void free_stim(gatspi_ctx* c) {
   dfree(c->d_edge_ptr); dfree(c->d_edge_time); dfree(c->d_init_in);
+  c->cap_edge_ptr = c->cap_edge_time = c->cap_init_in = 0;
+}
+
+// Copy n elements to a device buffer, reallocating only when it is too small.
+template <class T>
+int upload_reuse(gatspi_ctx* ctx, T*& dst, size_t& cap, const T* src, size_t n) {
+  if (!dst || cap < std::max<size_t>(n, 1)) {
+    dfree(dst);
+    cap = 0;
+    CK(cudaMalloc(&dst, std::max<size_t>(n, 1) * sizeof(T)));
+    cap = std::max<size_t>(n, 1);
+  }
+  if (src && n) CK(cudaMemcpy(dst, src, n * sizeof(T), cudaMemcpyHostToDevice));
+  return GATSPI_OK;
 }
 
 void free_arena(gatspi_ctx* c) {
@@ -336,15 +351,15 @@ int gatspi_set_stimulus(gatspi_ctx* ctx, int32_t num_cycles, int32_t cycle_ps, c
   CK(cudaSetDevice(ctx->device));
   const int64_t n = (int64_t)ctx->I * num_cycles;
   ctx->have_stim = ctx->have_result = false;
-  free_stim(ctx);
   ctx->C = num_cycles;
   ctx->L = cycle_ps;
   ctx->edge_ptr.assign(edge_ptr, edge_ptr + n + 1);
   ctx->init_in.assign(init, init + ctx->I);
   int rc;
-  if ((rc = upload(ctx, ctx->d_edge_ptr, edge_ptr, (size_t)n + 1))) return rc;
-  if ((rc = upload(ctx, ctx->d_edge_time, edge_time, (size_t)edge_ptr[n]))) return rc;
-  if ((rc = upload(ctx, ctx->d_init_in, init, (size_t)ctx->I))) return rc;
+  // device buffers are kept and reused while they are large enough
+  if ((rc = upload_reuse(ctx, ctx->d_edge_ptr, ctx->cap_edge_ptr, edge_ptr, (size_t)n + 1))) return rc;
+  if ((rc = upload_reuse(ctx, ctx->d_edge_time, ctx->cap_edge_time, edge_time, (size_t)edge_ptr[n]))) return rc;
+  if ((rc = upload_reuse(ctx, ctx->d_init_in, ctx->cap_init_in, init, (size_t)ctx->I))) return rc;
   ctx->have_stim = true;
   return GATSPI_OK;
 }

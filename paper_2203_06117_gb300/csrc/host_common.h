@@ -7,6 +7,7 @@
 #include <algorithm>
 #include <cstdint>
 #include <string>
+#include <thread>
 #include <vector>
 
 namespace gatspi_host {
@@ -152,6 +153,34 @@ inline std::string prepare_delays(const Prepared& r, const int32_t* gate_delay, 
   return "";
 }
 
+// Checks one range of (input, cycle) slots; returns the first bad slot and
+// why (0 = fine) in *bad / *kind.
+inline void validate_slots(int64_t k0, int64_t k1, int32_t L, const int64_t* edge_ptr, const int32_t* edge_time,
+                           int64_t* bad, int* kind) {
+  *bad = -1;
+  *kind = 0;
+  for (int64_t k = k0; k < k1; ++k) {
+    const int64_t a = edge_ptr[k], b = edge_ptr[k + 1];
+    if (b < a) {
+      *bad = k;
+      *kind = 1;
+      return;
+    }
+    int32_t prev = -1;
+    for (int64_t e = a; e < b; ++e) {
+      const int32_t t = edge_time[e];
+      if (t < 0 || t >= L || t <= prev) {
+        *bad = k;
+        *kind = (t < 0 || t >= L) ? 2 : 3;
+        return;
+      }
+      prev = t;
+    }
+  }
+}
+
+// Validates a stimulus; the (input, cycle) slots are checked by up to 16
+// host threads (the first bad slot is reported, as a serial scan would).
 inline std::string validate_stimulus(int32_t I, int32_t C, int32_t L, const uint8_t* init,
                                      const int64_t* edge_ptr, const int32_t* edge_time) {
   if (C < 1 || L < 1) return "num_cycles and cycle_ps must be >= 1";
@@ -159,16 +188,23 @@ inline std::string validate_stimulus(int32_t I, int32_t C, int32_t L, const uint
   const int64_t n = (int64_t)I * C;
   if (edge_ptr[0] != 0) return "edge_ptr[0] must be 0";
   if (edge_ptr[n] > 0 && !edge_time) return "null edge_time";
-  for (int64_t k = 0; k < n; ++k) {
-    const int64_t a = edge_ptr[k], b = edge_ptr[k + 1];
-    if (b < a) return "edge_ptr must be non-decreasing";
-    for (int64_t e = a; e < b; ++e) {
-      const int32_t t = edge_time[e];
-      if (t < 0 || t >= L)
-        return "edge time outside [0, cycle_ps) for input " + std::to_string(k / C) + " cycle " +
-               std::to_string(k % C);
-      if (e > a && t <= edge_time[e - 1]) return "edge times must increase strictly within a cycle";
-    }
+  const int nt = (int)std::max<int64_t>(1, std::min<int64_t>({16, (int64_t)std::thread::hardware_concurrency(),
+                                                               n / 65536 + 1}));
+  std::vector<int64_t> bad(nt, -1);
+  std::vector<int> kind(nt, 0);
+  std::vector<std::thread> pool;
+  for (int w = 1; w < nt; ++w)
+    pool.emplace_back(validate_slots, n * w / nt, n * (w + 1) / nt, L, edge_ptr, edge_time, &bad[w], &kind[w]);
+  validate_slots(0, n / nt, L, edge_ptr, edge_time, &bad[0], &kind[0]);
+  for (auto& t : pool) t.join();
+  for (int w = 0; w < nt; ++w) {
+    if (bad[w] < 0) continue;
+    const int64_t k = bad[w];
+    if (kind[w] == 1) return "edge_ptr must be non-decreasing";
+    if (kind[w] == 2)
+      return "edge time outside [0, cycle_ps) for input " + std::to_string(k / C) + " cycle " +
+             std::to_string(k % C);
+    return "edge times must increase strictly within a cycle";
   }
   for (int32_t i = 0; i < I; ++i)
     if (init[i] > 1) return "initial values must be 0 or 1";
