@@ -77,7 +77,9 @@ typedef struct gatspi_opts {
   int32_t items_per_thread; /* consecutive windows of one gate per thread:
                                1, 2, 4 or 8 (at most 4 with 512 threads);
                                0 = autotuned (see tile_items) or 4 */
-  int32_t reserved[3];   /* must be 0 */
+  int32_t digest;        /* 1 = also reduce every (net, window) waveform to a
+                            per-net 64-bit digest (gatspi_digest) */
+  int32_t reserved[2];   /* must be 0 */
 } gatspi_opts;
 
 /* Figures of the last gatspi_simulate call. */
@@ -188,6 +190,21 @@ int gatspi_simulate(gatspi_ctx* ctx, const gatspi_opts* opts);
  * Any pointer may be NULL.  Errors: ESTATE (nothing simulated).
  */
 int gatspi_saif(gatspi_ctx* ctx, int64_t* t0, int64_t* t1, int64_t* tc);
+
+/*
+ * Per-net digest of every waveform of the last gatspi_simulate run with
+ * opts.digest = 1 (the check of bit-exactness at scale: one number per net
+ * covers all its windows).  For net n and window w (global index) with
+ * start value v and edge times t_1..t_c:
+ *   h = mix(v + 1);  h = mix(h + 0x9E3779B97F4A7C15 + (uint32)t_k) for k = 1..c;
+ *   digest[n] = sum over windows of mix(h ^ mix(w + 1))   (mod 2^64)
+ * where mix is the SplitMix64 output function (Steele, Lea, Flood 2014):
+ *   z = (z ^ z >> 30) * 0xBF58476D1CE4E5B9; z = (z ^ z >> 27) *
+ *   0x94D049BB133111EB; z ^ z >> 31.
+ * The sum is order-free, so windows may be reduced in any order.  out is
+ * [I+G] in the caller's net order.  Errors: ESTATE (no digest computed).
+ */
+int gatspi_digest(gatspi_ctx* ctx, uint64_t* out);
 
 /*
  * Waveforms of every net in window `window` of the last simulation.  Only

@@ -41,7 +41,7 @@ _NAMES = {EINVAL: "EINVAL", ENOMEM: "ENOMEM", ECAPACITY: "ECAPACITY", ECUDA: "EC
 #: every entry point declared in include/gatspi.h
 EXPORTS = ["gatspi_create", "gatspi_destroy", "gatspi_last_error", "gatspi_load_netlist",
            "gatspi_load_delays", "gatspi_set_edit", "gatspi_set_stimulus", "gatspi_simulate", "gatspi_saif",
-           "gatspi_read_window", "gatspi_get_stats",
+           "gatspi_read_window", "gatspi_get_stats", "gatspi_digest",
            "gatspi_engine_create", "gatspi_engine_destroy", "gatspi_engine_last_error",
            "gatspi_engine_add_netlist", "gatspi_engine_submit", "gatspi_engine_step",
            "gatspi_engine_drain", "gatspi_engine_poll", "gatspi_engine_release",
@@ -81,7 +81,8 @@ def build(force: bool = False, nvcc: str = "nvcc") -> str:
 class gatspi_opts(ctypes.Structure):
     _fields_ = [("window_cycles", ctypes.c_int32), ("batch_windows", ctypes.c_int32),
                 ("tile_items", ctypes.c_int32), ("time_kernels", ctypes.c_int32),
-                ("items_per_thread", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+                ("items_per_thread", ctypes.c_int32), ("digest", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 2)]
 
 
 class gatspi_engine_opts(ctypes.Structure):
@@ -229,10 +230,17 @@ def gatspi_set_stimulus(ctx, num_cycles, cycle_ps, init, edge_ptr, edge_time) ->
 
 
 def gatspi_simulate(ctx, window_cycles=0, batch_windows=0, tile_items=0, time_kernels=0,
-                    items_per_thread=0) -> None:
+                    items_per_thread=0, digest=0) -> None:
     o = gatspi_opts(int(window_cycles), int(batch_windows), int(tile_items), int(time_kernels),
-                    int(items_per_thread))
+                    int(items_per_thread), int(digest))
     _check(ctx, lib().gatspi_simulate(ctx, ctypes.byref(o)))
+
+
+def gatspi_digest(ctx, num_nets: int):
+    """Per-net uint64 waveform digest of the last simulation run with digest=1."""
+    out = np.empty(num_nets, np.uint64)
+    _check(ctx, lib().gatspi_digest(ctx, _ptr(out)))
+    return out
 
 
 def gatspi_saif(ctx, num_nets: int):
@@ -286,6 +294,9 @@ class Simulator:
 
     def window(self, w: int):
         return gatspi_read_window(self.ctx, w, self.N)
+
+    def digest(self):
+        return gatspi_digest(self.ctx, self.N)
 
     def stats(self) -> dict:
         return gatspi_get_stats(self.ctx)

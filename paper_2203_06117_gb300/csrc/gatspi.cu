@@ -65,6 +65,8 @@ struct gatspi_ctx {
   // SAIF and status
   unsigned long long* d_t1 = nullptr;
   unsigned long long* d_tc = nullptr;
+  unsigned long long* d_digest = nullptr;  // [N] waveform digests (opts.digest)
+  bool have_digest = false;
   int32_t* d_status = nullptr;
   long long* d_in_prefix = nullptr;
   int64_t total_time = 0;
@@ -125,7 +127,8 @@ void free_netlist(gatspi_ctx* c) {
   c->max_edit = 0;
   dfree(c->d_fanin_ptr); dfree(c->d_fanin_net); dfree(c->d_net_level); dfree(c->d_lut);
   dfree(c->d_gate_desc);
-  dfree(c->d_gate_delay); dfree(c->d_wire_delay); dfree(c->d_t1); dfree(c->d_tc);
+  dfree(c->d_gate_delay); dfree(c->d_wire_delay); dfree(c->d_t1); dfree(c->d_tc); dfree(c->d_digest);
+  c->have_digest = false;
   dfree(c->d_in_prefix);
 }
 
@@ -284,6 +287,7 @@ int gatspi_load_netlist(gatspi_ctx* ctx, int32_t num_inputs, int32_t num_gates,
   if ((rc = upload(ctx, ctx->d_lut, ctx->lut.data(), ctx->lut.size()))) return rc;
   if ((rc = upload<unsigned long long>(ctx, ctx->d_t1, nullptr, ctx->N))) return rc;
   if ((rc = upload<unsigned long long>(ctx, ctx->d_tc, nullptr, ctx->N))) return rc;
+  if ((rc = upload<unsigned long long>(ctx, ctx->d_digest, nullptr, ctx->N))) return rc;
   if ((rc = upload<long long>(ctx, ctx->d_in_prefix, nullptr, ctx->I))) return rc;
   ctx->have_netlist = true;
   return GATSPI_OK;
@@ -375,8 +379,9 @@ int simulate_impl(gatspi_ctx* ctx, const gatspi_opts* opts) {
   CK(cudaSetDevice(ctx->device));
   gatspi_opts o{};
   if (opts) o = *opts;
-  for (int k = 0; k < 3; ++k)
+  for (int k = 0; k < 2; ++k)
     if (o.reserved[k]) return fail(ctx, GATSPI_EINVAL, "reserved option fields must be 0");
+  if (o.digest < 0 || o.digest > 1) return fail(ctx, GATSPI_EINVAL, "digest must be 0 or 1");
   const int32_t W = o.window_cycles ? o.window_cycles : 1;
   if (W < 1) return fail(ctx, GATSPI_EINVAL, "window_cycles must be >= 1");
   const int nt = o.tile_items ? o.tile_items : 256;
@@ -408,6 +413,8 @@ int simulate_impl(gatspi_ctx* ctx, const gatspi_opts* opts) {
   st.levels = ctx->D;
   CK(cudaMemsetAsync(ctx->d_t1, 0, sizeof(unsigned long long) * ctx->N, ctx->stream));
   CK(cudaMemsetAsync(ctx->d_tc, 0, sizeof(unsigned long long) * ctx->N, ctx->stream));
+  CK(cudaMemsetAsync(ctx->d_digest, 0, sizeof(unsigned long long) * ctx->N, ctx->stream));
+  ctx->have_digest = false;
   const size_t n_ev = (size_t)2 * (ctx->D + 2);
   if (o.time_kernels && ctx->ev.size() < n_ev) {
     for (auto e : ctx->ev) cudaEventDestroy(e);
@@ -501,6 +508,19 @@ int simulate_impl(gatspi_ctx* ctx, const gatspi_opts* opts) {
       st.items += p.seg.n_items;
     }
     if (o.time_kernels) CK(cudaEventRecord(ev_last, ctx->stream));
+    if (o.digest) {  // after the timed region: the digest reads every waveform of the batch once
+      DigestParams q{};
+      q.rmeta = ctx->d_rmeta; q.tinfo = ctx->d_tinfo; q.rstart = ctx->d_rstart;
+      q.net_level = ctx->d_net_level; q.lvl_base = ctx->d_lvl_base; q.times = ctx->d_times;
+      q.capacity = ctx->times_cap; q.out = ctx->d_digest; q.status = ctx->d_status;
+      q.N = ctx->N; q.NW = nw; q.w0 = w0;
+      q.TW = ctx->batch_T > 0 ? ctx->batch_TW : 128;
+      q.T = (nw + q.TW - 1) / q.TW;
+      const long long warps = (long long)q.N * q.T;
+      digest_kernel<<<(unsigned)((warps + 7) / 8), 256, 0, ctx->stream>>>(q);
+      CK(cudaGetLastError());
+      st.kernel_launches++;
+    }
     int32_t status = 0;
     long long lvl_end = 0;
     CK(cudaMemcpyAsync(&status, ctx->d_status, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream));
@@ -531,6 +551,7 @@ int simulate_impl(gatspi_ctx* ctx, const gatspi_opts* opts) {
       st.levels = ctx->D;
       CK(cudaMemsetAsync(ctx->d_t1, 0, sizeof(unsigned long long) * ctx->N, ctx->stream));
       CK(cudaMemsetAsync(ctx->d_tc, 0, sizeof(unsigned long long) * ctx->N, ctx->stream));
+      CK(cudaMemsetAsync(ctx->d_digest, 0, sizeof(unsigned long long) * ctx->N, ctx->stream));
       continue;
     }
     if (o.time_kernels) {
@@ -576,6 +597,7 @@ int simulate_impl(gatspi_ctx* ctx, const gatspi_opts* opts) {
   st.items_per_thread = ipt;
   ctx->stats = st;
   ctx->have_result = true;
+  ctx->have_digest = o.digest != 0;
   return GATSPI_OK;
 }
 
@@ -652,6 +674,16 @@ int gatspi_saif(gatspi_ctx* ctx, int64_t* t0, int64_t* t1, int64_t* tc) {
     if (t0) t0[e] = ctx->total_time - (int64_t)a[n];
     if (tc) tc[e] = (int64_t)b[n];
   }
+  return GATSPI_OK;
+}
+
+int gatspi_digest(gatspi_ctx* ctx, uint64_t* out) {
+  if (!ctx || !out) return GATSPI_EINVAL;
+  if (!ctx->have_digest) return fail(ctx, GATSPI_ESTATE, "no digest: simulate with opts.digest = 1 first");
+  CK(cudaSetDevice(ctx->device));
+  std::vector<unsigned long long> d(ctx->N);
+  CK(cudaMemcpy(d.data(), ctx->d_digest, sizeof(unsigned long long) * ctx->N, cudaMemcpyDeviceToHost));
+  for (int32_t e = 0; e < ctx->N; ++e) out[e] = d[ctx->net_int[e]];
   return GATSPI_OK;
 }
 

@@ -266,3 +266,51 @@ def test_planted_mistake_is_caught(mutation):
     fails += _settled_failures(wl, 1, mutation)
     fails += _invariant_failures(wl, 1, mutation)
     assert fails, f"planted mistake '{mutation}' passes every pin"
+
+
+# ---------------------------------------------------------------- digests
+# The per-net waveform digest (oracle/digest.py) checks bit-exactness at
+# scale.  Its mixing function is the SplitMix64 output function; the
+# generator module implements the same published function independently in
+# C (its counter-keyed draws), which pins the oracle's version.
+
+from oracle import digest as odig  # noqa: E402
+
+_G = 0x9E3779B97F4A7C15
+_C2 = 0xD1B54A32D192ED03
+
+
+@pytest.mark.parametrize("seed,stream,idx", [(1, 0, 0), (7, 3, 12345), (2**63 + 5, 17, 2**40 + 3)])
+def test_digest_mix_matches_generator_splitmix(seed, stream, idx):
+    m = 2**64 - 1
+    a = int(odig.mix(np.array([(seed + _G * (stream + 1)) & m], np.uint64))[0])
+    x = int(odig.mix(np.array([a ^ ((idx * _C2 + _G) & m)], np.uint64))[0])
+    assert x == gen.draw(seed, stream, idx)
+
+
+def test_digest_empty_waveform_closed_form():
+    init = np.array([0, 1], np.uint8)
+    ptr = np.array([0, 0, 0], np.int64)
+    t = odig.window_terms(init, ptr, np.zeros(0, np.int32), 41)
+    mw = odig.mix(np.array([42], np.uint64))[0]
+    for n, v in enumerate((0, 1)):
+        h = odig.mix(np.array([v + 1], np.uint64))[0]
+        assert t[n] == odig.mix(np.array([h ^ mw], np.uint64))[0]
+
+
+def test_digest_is_order_free_and_local():
+    wl = gen.make_workload("tiny", seed=4, num_cycles=40)
+    sim = oracle.EventSim(wl.netlist, wl.delays, wl.stim, W=1)
+    fwd = odig.digest(sim, range(40))
+    rev = odig.digest(sim, reversed(range(40)))
+    assert np.array_equal(fwd, rev)
+    # one changed edge time changes exactly one net's term
+    init, ptr, times = sim.window(7)
+    base = odig.window_terms(init, ptr, times, 7)
+    n = int(np.nonzero(np.diff(ptr) > 0)[0][0])
+    times2 = times.copy()
+    times2[ptr[n]] += 1
+    moved = odig.window_terms(init, ptr, times2, 7)
+    assert np.count_nonzero(moved != base) == 1 and moved[n] != base[n]
+    # the window index enters: the same waveforms at another index differ
+    assert not np.array_equal(odig.window_terms(init, ptr, times, 8), base)
