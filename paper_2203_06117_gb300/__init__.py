@@ -28,7 +28,7 @@ ROOT = os.path.dirname(_HERE)
 LIB_PATH = os.path.join(_HERE, "_build", "libgatspi.so")
 INCLUDE = os.path.join(ROOT, "include")
 SOURCES = [os.path.join(_HERE, "csrc", f) for f in ("gatspi.cu", "engine.cu", "noalloc.cu")]
-DEPS = SOURCES + [os.path.join(_HERE, "csrc", f) for f in ("kernels.cuh", "host_common.h")] + \
+DEPS = SOURCES + [os.path.join(_HERE, "csrc", f) for f in ("kernels.cuh", "digest.cuh", "host_common.h")] + \
     [os.path.join(INCLUDE, "gatspi.h")]
 
 NVCC_FLAGS = ["-Xcompiler", "-fPIC", "-std=c++17",

@@ -13,6 +13,7 @@
 #include "gatspi.h"
 #include "host_common.h"
 #include "kernels.cuh"
+#include "digest.cuh"
 
 using namespace gatspi_dev;
 
@@ -68,6 +69,16 @@ struct gatspi_ctx {
   unsigned long long* d_digest = nullptr;  // [N] waveform digests (opts.digest)
   bool have_digest = false;
   int32_t* d_status = nullptr;
+  // pinned host words the batch's copies use (so a batch can be captured
+  // into a CUDA graph): input prefixes, then status and the level end
+  long long* h_in_prefix = nullptr;
+  long long* h_ret = nullptr;  // [0] status, [1] edges of the batch
+  // the last batch captured into a graph, replayed while nothing it bakes
+  // in changes (shape, stimulus, buffers)
+  cudaGraphExec_t gexec = nullptr;
+  std::vector<long long> gkey;
+  int64_t generation = 0;      // bumped by every load/edit/stimulus call
+  int eager_nt = 0, eager_ipt = 0;  // a launch shape already run eagerly
   long long* d_in_prefix = nullptr;
   int64_t total_time = 0;
 
@@ -227,7 +238,8 @@ int gatspi_create(gatspi_ctx** out, int device, size_t arena_bytes) {
   ctx->device = device;
   if (cudaSetDevice(device) != cudaSuccess ||
       cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaMalloc(&ctx->d_status, sizeof(int32_t)) != cudaSuccess) {
+      cudaMalloc(&ctx->d_status, sizeof(int32_t)) != cudaSuccess ||
+      cudaMallocHost(&ctx->h_ret, 2 * sizeof(long long)) != cudaSuccess) {
     cudaGetLastError();
     delete ctx;
     return GATSPI_ECUDA;
@@ -247,6 +259,9 @@ int gatspi_destroy(gatspi_ctx* ctx) {
   free_stim(ctx);
   free_arena(ctx);
   dfree(ctx->d_status);
+  if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
+  if (ctx->h_in_prefix) cudaFreeHost(ctx->h_in_prefix);
+  if (ctx->h_ret) cudaFreeHost(ctx->h_ret);
   for (auto e : ctx->ev) cudaEventDestroy(e);
   if (ctx->stream) cudaStreamDestroy(ctx->stream);
   delete ctx;
@@ -258,6 +273,7 @@ const char* gatspi_last_error(gatspi_ctx* ctx) { return ctx ? ctx->err.c_str() :
 int gatspi_load_netlist(gatspi_ctx* ctx, int32_t num_inputs, int32_t num_gates,
                         const int32_t* fanin_ptr, const int32_t* fanin_net, const uint16_t* lut) {
   if (!ctx) return GATSPI_EINVAL;
+  ctx->generation++;
   gatspi_host::Prepared r;
   const std::string why = gatspi_host::prepare_netlist(num_inputs, num_gates, fanin_ptr, fanin_net, lut, &r);
   if (!why.empty()) return fail(ctx, GATSPI_EINVAL, why);
@@ -289,12 +305,16 @@ int gatspi_load_netlist(gatspi_ctx* ctx, int32_t num_inputs, int32_t num_gates,
   if ((rc = upload<unsigned long long>(ctx, ctx->d_tc, nullptr, ctx->N))) return rc;
   if ((rc = upload<unsigned long long>(ctx, ctx->d_digest, nullptr, ctx->N))) return rc;
   if ((rc = upload<long long>(ctx, ctx->d_in_prefix, nullptr, ctx->I))) return rc;
+  if (ctx->h_in_prefix) cudaFreeHost(ctx->h_in_prefix);
+  ctx->h_in_prefix = nullptr;
+  CK(cudaMallocHost(&ctx->h_in_prefix, sizeof(long long) * std::max<int32_t>(ctx->I, 1)));
   ctx->have_netlist = true;
   return GATSPI_OK;
 }
 
 int gatspi_load_delays(gatspi_ctx* ctx, const int32_t* gate_delay, const int32_t* wire_delay) {
   if (!ctx) return GATSPI_EINVAL;
+  ctx->generation++;
   if (!ctx->have_netlist) return fail(ctx, GATSPI_ESTATE, "load a netlist before its delays");
   gatspi_host::Prepared view;  // only the fields prepare_delays reads
   view.G = ctx->G; view.P = ctx->P;
@@ -319,6 +339,7 @@ int gatspi_load_delays(gatspi_ctx* ctx, const int32_t* gate_delay, const int32_t
 
 int gatspi_set_edit(gatspi_ctx* ctx, int32_t n_edits, const int32_t* edit_gate, const int32_t* edit_delta) {
   if (!ctx) return GATSPI_EINVAL;
+  ctx->generation++;
   if (!ctx->have_delays) return fail(ctx, GATSPI_ESTATE, "load delays before an edit");
   if (n_edits < 0 || (n_edits > 0 && (!edit_gate || !edit_delta)))
     return fail(ctx, GATSPI_EINVAL, "bad delay edit arrays");
@@ -348,6 +369,7 @@ int gatspi_set_edit(gatspi_ctx* ctx, int32_t n_edits, const int32_t* edit_gate, 
 int gatspi_set_stimulus(gatspi_ctx* ctx, int32_t num_cycles, int32_t cycle_ps, const uint8_t* init,
                         const int64_t* edge_ptr, const int32_t* edge_time) {
   if (!ctx) return GATSPI_EINVAL;
+  ctx->generation++;
   if (!ctx->have_netlist) return fail(ctx, GATSPI_ESTATE, "load a netlist before the stimulus");
   const std::string why =
       gatspi_host::validate_stimulus(ctx->I, num_cycles, cycle_ps, init, edge_ptr, edge_time);
@@ -457,76 +479,126 @@ int simulate_impl(gatspi_ctx* ctx, const gatspi_opts* opts) {
       if (NW > 1) { NW = (NW + 1) / 2; continue; }
       return fail(ctx, GATSPI_ECAPACITY, "input edges of one window exceed the arena");
     }
-    CK(cudaMemcpyAsync(ctx->d_in_prefix, in_prefix.data(), sizeof(long long) * ctx->I,
-                       cudaMemcpyHostToDevice, ctx->stream));
-    if (o.time_kernels && !first_recorded) {
-      CK(cudaEventRecord(ev_first, ctx->stream));
-      first_recorded = true;
+    for (int32_t i = 0; i < ctx->I; ++i) ctx->h_in_prefix[i] = in_prefix[i];
+    const bool record_first = o.time_kernels && !first_recorded;
+    // everything the batch puts on the stream; captured into a CUDA graph
+    // and replayed when the same batch comes again (repeated simulations of
+    // one stimulus), launched eagerly otherwise.  Timing events are recorded
+    // as external events so that a replayed graph still times its kernels.
+    auto enqueue = [&](bool capturing) -> cudaError_t {
+      cudaError_t e;
+      auto rec = [&](cudaEvent_t ev) {
+        return capturing ? cudaEventRecordWithFlags(ev, ctx->stream, cudaEventRecordExternal)
+                         : cudaEventRecord(ev, ctx->stream);
+      };
+      if ((e = cudaMemcpyAsync(ctx->d_in_prefix, ctx->h_in_prefix, sizeof(long long) * ctx->I,
+                               cudaMemcpyHostToDevice, ctx->stream)))
+        return e;
+      if (record_first && (e = rec(ev_first))) return e;
+      if ((e = cudaMemsetAsync(ctx->d_counters, 0, ctx->scratch_bytes, ctx->stream))) return e;
+      if ((e = cudaMemsetAsync(ctx->d_status, 0, sizeof(int32_t), ctx->stream))) return e;
+      {
+        InputParams q{};
+        q.edge_ptr = ctx->d_edge_ptr; q.edge_time = ctx->d_edge_time; q.init_in = ctx->d_init_in;
+        q.in_prefix = ctx->d_in_prefix; q.rstart = ctx->d_rstart; q.rmeta = ctx->d_rmeta; q.times = ctx->d_times;
+        q.tinfo = ctx->d_tinfo; q.T = ctx->batch_T; q.TW = ctx->batch_TW;
+        q.saif_t1 = ctx->d_t1; q.saif_tc = ctx->d_tc; q.total = l0; q.lvl_base = ctx->d_lvl_base;
+        q.status = ctx->d_status;
+        q.I = ctx->I; q.NW = nw; q.w0 = w0; q.W = W; q.C = ctx->C; q.L = ctx->L;
+        q.n_items = ctx->I * nw;
+        if (o.time_kernels && (e = rec(ctx->ev[0]))) return e;
+        inputs_kernel<<<(q.n_items + 255) / 256, 256, 0, ctx->stream>>>(q);
+        if ((e = cudaGetLastError())) return e;
+        if (o.time_kernels && (e = rec(ctx->ev[1]))) return e;
+      }
+      JobView job{};
+      job.fanin_ptr = ctx->d_fanin_ptr; job.fanin_net = ctx->d_fanin_net; job.lut = ctx->d_lut;
+      job.gate_delay = ctx->d_gate_delay; job.wire_delay = ctx->d_wire_delay;
+      job.net_level = ctx->d_net_level; job.gate_delta = ctx->d_gate_delta;
+      job.gdesc = (const int4*)ctx->d_gate_desc;
+      job.rstart = ctx->d_rstart; job.tinfo = ctx->d_tinfo; job.T = ctx->batch_T; job.rmeta = ctx->d_rmeta;
+      job.times = ctx->d_times; job.lvl_base = ctx->d_lvl_base;
+      job.capacity = ctx->times_cap; job.saif_t1 = ctx->d_t1; job.saif_tc = ctx->d_tc;
+      job.status = ctx->d_status;
+      job.I = ctx->I; job.NW = nw; job.w0 = w0; job.W = W; job.C = ctx->C; job.L = ctx->L;
+      for (int32_t l = 1; l <= ctx->D; ++l) {
+        PropParams p{};
+        p.job = job;
+        p.seg.counters = ctx->d_counters + l;
+        p.seg.level = l;
+        p.seg.gate_begin = ctx->lvl_gate_begin[l];
+        p.seg.n_items = (ctx->lvl_gate_begin[l + 1] - ctx->lvl_gate_begin[l]) * nw;
+        p.seg.n_tiles = (int32_t)level_tiles(ctx->lvl_gate_begin[l + 1] - ctx->lvl_gate_begin[l], nw, ipt);
+        p.tile_counter = ctx->d_tile_counter + l;
+        if (o.time_kernels && (e = rec(ctx->ev[2 * l]))) return e;
+        SingleLaunch go{&p, ctx->stream};
+        launch_variant(nt, ipt, go);
+        if ((e = cudaGetLastError())) return e;
+        if (o.time_kernels && (e = rec(ctx->ev[2 * l + 1]))) return e;
+      }
+      if (o.time_kernels && (e = rec(ev_last))) return e;
+      if (o.digest) {  // after the timed region: the digest reads every waveform of the batch once
+        DigestParams q{};
+        q.rmeta = ctx->d_rmeta; q.tinfo = ctx->d_tinfo; q.rstart = ctx->d_rstart;
+        q.net_level = ctx->d_net_level; q.lvl_base = ctx->d_lvl_base; q.times = ctx->d_times;
+        q.capacity = ctx->times_cap; q.out = ctx->d_digest; q.status = ctx->d_status;
+        q.N = ctx->N; q.NW = nw; q.w0 = w0;
+        q.TW = ctx->batch_T > 0 ? ctx->batch_TW : 128;
+        q.T = (nw + q.TW - 1) / q.TW;
+        const long long warps = (long long)q.N * q.T;
+        digest_kernel<<<(unsigned)((warps + 7) / 8), 256, 0, ctx->stream>>>(q);
+        if ((e = cudaGetLastError())) return e;
+      }
+      if ((e = cudaMemcpyAsync(&ctx->h_ret[0], ctx->d_status, sizeof(int32_t), cudaMemcpyDeviceToHost,
+                               ctx->stream)))
+        return e;
+      return cudaMemcpyAsync(&ctx->h_ret[1], ctx->d_lvl_base + ctx->D + 1, sizeof(long long),
+                             cudaMemcpyDeviceToHost, ctx->stream);
+    };
+    ctx->h_ret[0] = 0;
+    // a graph bakes in pointers, sizes and per-batch values: replay it only
+    // while all of them are the same
+    const std::vector<long long> key = {
+        ctx->generation, (long long)(uintptr_t)ctx->d_arena, (long long)ctx->arena_bytes, ctx->times_cap,
+        nw, w0, W, nt, ipt, o.digest, o.time_kernels, record_first ? 1 : 0, l0, ctx->batch_T,
+        (long long)(uintptr_t)ctx->d_gate_delta};
+    bool done = false;
+    if (ctx->eager_nt == nt && ctx->eager_ipt == ipt) {  // the variant's attributes are set
+      if (!(ctx->gexec && ctx->gkey == key)) {
+        if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
+        ctx->gexec = nullptr;
+        ctx->gkey.clear();
+        cudaGraph_t graph = nullptr;
+        if (cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+          const cudaError_t ce = enqueue(true);
+          const cudaError_t ee = cudaStreamEndCapture(ctx->stream, &graph);
+          if (ce == cudaSuccess && ee == cudaSuccess && graph &&
+              cudaGraphInstantiate(&ctx->gexec, graph, 0) == cudaSuccess) {
+            ctx->gkey = key;
+          } else {
+            ctx->gexec = nullptr;
+          }
+          if (graph) cudaGraphDestroy(graph);
+        }
+        cudaGetLastError();  // a capture that failed leaves the eager path below
+      }
+      if (ctx->gexec) {
+        CK(cudaGraphLaunch(ctx->gexec, ctx->stream));
+        done = true;
+      }
     }
-    CK(cudaMemsetAsync(ctx->d_counters, 0, ctx->scratch_bytes, ctx->stream));
-    CK(cudaMemsetAsync(ctx->d_status, 0, sizeof(int32_t), ctx->stream));
-    {
-      InputParams q{};
-      q.edge_ptr = ctx->d_edge_ptr; q.edge_time = ctx->d_edge_time; q.init_in = ctx->d_init_in;
-      q.in_prefix = ctx->d_in_prefix; q.rstart = ctx->d_rstart; q.rmeta = ctx->d_rmeta; q.times = ctx->d_times;
-      q.tinfo = ctx->d_tinfo; q.T = ctx->batch_T; q.TW = ctx->batch_TW;
-      q.saif_t1 = ctx->d_t1; q.saif_tc = ctx->d_tc; q.total = l0; q.lvl_base = ctx->d_lvl_base;
-      q.status = ctx->d_status;
-      q.I = ctx->I; q.NW = nw; q.w0 = w0; q.W = W; q.C = ctx->C; q.L = ctx->L;
-      q.n_items = ctx->I * nw;
-      if (o.time_kernels) CK(cudaEventRecord(ctx->ev[0], ctx->stream));
-      inputs_kernel<<<(q.n_items + 255) / 256, 256, 0, ctx->stream>>>(q);
-      CK(cudaGetLastError());
-      if (o.time_kernels) CK(cudaEventRecord(ctx->ev[1], ctx->stream));
-      st.kernel_launches++;
+    if (!done) {
+      CK(enqueue(false));
+      ctx->eager_nt = nt;
+      ctx->eager_ipt = ipt;
     }
-    JobView job{};
-    job.fanin_ptr = ctx->d_fanin_ptr; job.fanin_net = ctx->d_fanin_net; job.lut = ctx->d_lut;
-    job.gate_delay = ctx->d_gate_delay; job.wire_delay = ctx->d_wire_delay;
-    job.net_level = ctx->d_net_level; job.gate_delta = ctx->d_gate_delta;
-    job.gdesc = (const int4*)ctx->d_gate_desc;
-    job.rstart = ctx->d_rstart; job.tinfo = ctx->d_tinfo; job.T = ctx->batch_T; job.rmeta = ctx->d_rmeta; job.times = ctx->d_times; job.lvl_base = ctx->d_lvl_base;
-    job.capacity = ctx->times_cap; job.saif_t1 = ctx->d_t1; job.saif_tc = ctx->d_tc;
-    job.status = ctx->d_status;
-    job.I = ctx->I; job.NW = nw; job.w0 = w0; job.W = W; job.C = ctx->C; job.L = ctx->L;
-    for (int32_t l = 1; l <= ctx->D; ++l) {
-      PropParams p{};
-      p.job = job;
-      p.seg.counters = ctx->d_counters + l;
-      p.seg.level = l;
-      p.seg.gate_begin = ctx->lvl_gate_begin[l];
-      p.seg.n_items = (ctx->lvl_gate_begin[l + 1] - ctx->lvl_gate_begin[l]) * nw;
-      p.seg.n_tiles = (int32_t)level_tiles(ctx->lvl_gate_begin[l + 1] - ctx->lvl_gate_begin[l], nw, ipt);
-      p.tile_counter = ctx->d_tile_counter + l;
-      if (o.time_kernels) CK(cudaEventRecord(ctx->ev[2 * l], ctx->stream));
-      SingleLaunch go{&p, ctx->stream};
-      launch_variant(nt, ipt, go);
-      CK(cudaGetLastError());
-      if (o.time_kernels) CK(cudaEventRecord(ctx->ev[2 * l + 1], ctx->stream));
-      st.kernel_launches++;
-      st.prop_launches++;
-      st.items += p.seg.n_items;
-    }
-    if (o.time_kernels) CK(cudaEventRecord(ev_last, ctx->stream));
-    if (o.digest) {  // after the timed region: the digest reads every waveform of the batch once
-      DigestParams q{};
-      q.rmeta = ctx->d_rmeta; q.tinfo = ctx->d_tinfo; q.rstart = ctx->d_rstart;
-      q.net_level = ctx->d_net_level; q.lvl_base = ctx->d_lvl_base; q.times = ctx->d_times;
-      q.capacity = ctx->times_cap; q.out = ctx->d_digest; q.status = ctx->d_status;
-      q.N = ctx->N; q.NW = nw; q.w0 = w0;
-      q.TW = ctx->batch_T > 0 ? ctx->batch_TW : 128;
-      q.T = (nw + q.TW - 1) / q.TW;
-      const long long warps = (long long)q.N * q.T;
-      digest_kernel<<<(unsigned)((warps + 7) / 8), 256, 0, ctx->stream>>>(q);
-      CK(cudaGetLastError());
-      st.kernel_launches++;
-    }
-    int32_t status = 0;
-    long long lvl_end = 0;
-    CK(cudaMemcpyAsync(&status, ctx->d_status, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream));
-    CK(cudaMemcpyAsync(&lvl_end, ctx->d_lvl_base + ctx->D + 1, sizeof(long long), cudaMemcpyDeviceToHost,
-                       ctx->stream));
+    if (record_first) first_recorded = true;
+    st.kernel_launches += 1 + ctx->D + (o.digest ? 1 : 0);
+    st.prop_launches += ctx->D;
+    st.items += (int64_t)ctx->G * nw;
     CK(cudaStreamSynchronize(ctx->stream));
+    const int32_t status = (int32_t)ctx->h_ret[0];
+    const long long lvl_end = ctx->h_ret[1];
     if (status & kStTimeout) return fail(ctx, GATSPI_ETIMEOUT, "a device-side wait ran out");
     if (status & (kStCapacity | kStOffset | kStCorrupt)) {
       // undo this batch's SAIF contribution by re-running from scratch
