@@ -53,6 +53,8 @@ struct EJob {
   std::string err;
   cudaEvent_t done_ev = nullptr;
   bool done_recorded = false;
+  cudaEvent_t ready_ev = nullptr;  // the job's uploads are on the device
+  bool ready_waited = false;       // the compute stream already waits for it
 };
 
 struct PartResult {
@@ -89,6 +91,7 @@ struct EPart {
 struct gatspi_engine {
   int device = 0;
   cudaStream_t stream = nullptr;
+  cudaStream_t upload = nullptr;  // job uploads, off the compute stream
   std::string err;
   size_t budget = 0, in_use = 0;
   int64_t step_load = 0;  // average level items of the parts in flight
@@ -145,12 +148,16 @@ int eupload(gatspi_engine* eng, T*& dst, const T* src, size_t n) {
   return GATSPI_OK;
 }
 
-// Stream-ordered allocation and copy (the host buffer may be reused as soon
-// as this returns: pageable copies are staged before the call returns).
+// Stream-ordered allocation and copy on the upload stream (the host buffer
+// may be reused as soon as this returns: pageable copies are staged before
+// the call returns).  Copies from pageable memory wait for their stream to
+// drain first, so they go on a stream of their own: the compute stream
+// keeps running while a job is uploaded, and waits for the job's ready
+// event only before the job's first kernel.
 template <class T>
 int eupload_async(gatspi_engine* eng, T*& dst, const T* src, size_t n) {
-  ECK(cudaMallocAsync((void**)&dst, std::max<size_t>(n, 1) * sizeof(T), eng->stream));
-  if (src && n) ECK(cudaMemcpyAsync(dst, src, n * sizeof(T), cudaMemcpyHostToDevice, eng->stream));
+  ECK(cudaMallocAsync((void**)&dst, std::max<size_t>(n, 1) * sizeof(T), eng->upload));
+  if (src && n) ECK(cudaMemcpyAsync(dst, src, n * sizeof(T), cudaMemcpyHostToDevice, eng->upload));
   return GATSPI_OK;
 }
 
@@ -210,10 +217,17 @@ JobView make_view(const ENetlist& nl, const EJob& j, const EPart& p) {
 }
 
 void free_job_device(EJob& j, cudaStream_t s) {
+  // a job freed before its first kernel: its uploads may still be in flight
+  if (j.ready_ev && !j.ready_waited) {
+    cudaStreamWaitEvent(s, j.ready_ev, 0);
+    j.ready_waited = true;
+  }
   dfree_async(j.d_edge_ptr, s); dfree_async(j.d_edge_time, s); dfree_async(j.d_init_in, s);
   dfree_async(j.d_gate_delta, s); dfree_async(j.d_t1, s); dfree_async(j.d_tc, s);
   if (j.done_ev) cudaEventDestroy(j.done_ev);
   j.done_ev = nullptr;
+  if (j.ready_ev) cudaEventDestroy(j.ready_ev);
+  j.ready_ev = nullptr;
 }
 
 int fail_job(gatspi_engine* eng, EJob& j, int code, const std::string& why) {
@@ -347,6 +361,7 @@ int gatspi_engine_create(gatspi_engine** out, int device, size_t arena_bytes, co
   if (!eng->opts.step_items) eng->opts.step_items = 1ll << 25;
   if (cudaSetDevice(device) != cudaSuccess ||
       cudaStreamCreateWithFlags(&eng->stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&eng->upload, cudaStreamNonBlocking) != cudaSuccess ||
       cudaMalloc(&eng->d_counter, sizeof(int32_t) * (size_t)(eng->opts.max_active / kMaxSegs + 2)) !=
           cudaSuccess ||
       cudaMallocHost(&eng->h_results, sizeof(PartResult) * (size_t)eng->opts.max_active) != cudaSuccess) {
@@ -397,6 +412,8 @@ int gatspi_engine_destroy(gatspi_engine* eng) {
   dfree(eng->d_stage);
   dfree(eng->d_counter);
   if (eng->h_results) cudaFreeHost(eng->h_results);
+  if (eng->upload) cudaStreamSynchronize(eng->upload);
+  if (eng->upload) cudaStreamDestroy(eng->upload);
   if (eng->stream) cudaStreamDestroy(eng->stream);
   // hand the memory parked in the stream-ordered pool back to the device
   cudaMemPool_t pool;
@@ -478,8 +495,10 @@ int gatspi_engine_submit(gatspi_engine* eng, int32_t netlist_id, int32_t num_cyc
   if (n_edits > 0 && (rc = eupload_async(eng, j->d_gate_delta, delta.data(), delta.size()))) return undo(rc);
   if ((rc = eupload_async<unsigned long long>(eng, j->d_t1, nullptr, nl.r.N))) return undo(rc);
   if ((rc = eupload_async<unsigned long long>(eng, j->d_tc, nullptr, nl.r.N))) return undo(rc);
-  ECK(cudaMemsetAsync(j->d_t1, 0, sizeof(unsigned long long) * nl.r.N, eng->stream));
-  ECK(cudaMemsetAsync(j->d_tc, 0, sizeof(unsigned long long) * nl.r.N, eng->stream));
+  ECK(cudaMemsetAsync(j->d_t1, 0, sizeof(unsigned long long) * nl.r.N, eng->upload));
+  ECK(cudaMemsetAsync(j->d_tc, 0, sizeof(unsigned long long) * nl.r.N, eng->upload));
+  ECK(cudaEventCreateWithFlags(&j->ready_ev, cudaEventDisableTiming));
+  ECK(cudaEventRecord(j->ready_ev, eng->upload));
   // cut into parts of at most part_items (gate, window) items and a level
   // item count that fits int32
   int64_t widest = nl.r.I;
@@ -664,6 +683,10 @@ static int engine_step_impl(gatspi_engine* eng, int32_t* active_out, int32_t* qu
     q.total = l0;
     q.I = nl.r.I; q.NW = p.nw; q.w0 = p.w0; q.W = j.W; q.C = j.C; q.L = j.L;
     q.n_items = nl.r.I * p.nw;
+    if (!j.ready_waited) {  // the job's first kernel: its uploads must have landed
+      ECK(cudaStreamWaitEvent(eng->stream, j.ready_ev, 0));
+      j.ready_waited = true;
+    }
     inputs_kernel<<<(q.n_items + 255) / 256, 256, 0, eng->stream>>>(q);
     ECK(cudaGetLastError());
     eng->stats.kernel_launches++;

@@ -54,12 +54,17 @@ def _work(netlists, reqs):
 
 
 def run_batched(netlists, reqs, keep_results=True, **engine_opts):
-    """All jobs submitted at t=0, engine drained.  Returns (seconds, stats)."""
+    """All jobs available at t=0, engine drained.  Each submission (which
+    copies the job's stimulus to the device) is followed by one engine step,
+    so the device works on the jobs already admitted while later ones are
+    still being uploaded.  Returns (seconds, stats)."""
     with Engine(**engine_opts) as eng:
         ids = [eng.add_netlist(w.netlist, w.delays) for w in netlists]
         t0 = time.perf_counter()
-        jobs = [eng.submit(ids[r.netlist], r.stim, r.window_cycles, r.edit_gate, r.edit_delta)
-                for r in reqs]
+        jobs = []
+        for r in reqs:
+            jobs.append(eng.submit(ids[r.netlist], r.stim, r.window_cycles, r.edit_gate, r.edit_delta))
+            eng.step()
         eng.drain()
         for r, j in zip(reqs, jobs):
             state, saif = eng.poll(j, ids[r.netlist] if keep_results else None)
