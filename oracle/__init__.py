@@ -34,6 +34,7 @@ MUTATIONS = {
     "gate_cancel_on_equal": 3, "msi_lowest_pin": 4, "side_before_switch": 5,
     "row_transposed": 6, "t1_unclipped": 7, "window_init_from_cycle0": 8,
     "no_wire_filter": 9, "no_gate_filter": 10, "out_delay_from_old_y": 11,
+    "gate_stack_depth_one": 12, "wire_crossing_kept": 13,
 }
 
 
@@ -67,6 +68,8 @@ def _load():
         lib.osim_t1.argtypes = [vp, vp]
         lib.osim_saif.restype = i64
         lib.osim_saif.argtypes = [vp, i32, i32, vp, vp]
+        lib.osim_set_pulse.restype = i32
+        lib.osim_set_pulse.argtypes = [vp, i32, i32]
         _lib = lib
     return _lib
 
@@ -79,10 +82,14 @@ class EventSim:
     """Event-driven oracle over one netlist + delays + stimulus.
 
     ``W`` is the window length in cycles (each window starts from its
-    settled values and runs on its own time axis).
+    settled values and runs on its own time axis).  ``pulse_gate`` and
+    ``pulse_wire`` are the pulse limits (PATHPULSEPERCENT, 0..100) of the
+    gate and interconnect inertial tests; 100 is Algorithm 1 as printed,
+    0 transport delay (Section 3: other values edit the output test).
     """
 
-    def __init__(self, netlist, delays, stim, W: int = 1, mutation: str = "none"):
+    def __init__(self, netlist, delays, stim, W: int = 1, mutation: str = "none",
+                 pulse_gate: int = 100, pulse_wire: int = 100):
         self._lib = _load()
         # keep contiguous copies alive for the lifetime of the C object
         self._arrs = [np.ascontiguousarray(a) for a in (
@@ -100,6 +107,8 @@ class EventSim:
             MUTATIONS[mutation])
         if not self._h:
             raise ValueError("oracle: invalid netlist or stimulus")
+        if self._lib.osim_set_pulse(self._h, int(pulse_gate), int(pulse_wire)) != 0:
+            raise ValueError("oracle: pulse limits must be 0..100 percent")
 
     def __del__(self):
         h = getattr(self, "_h", None)

@@ -25,6 +25,15 @@ Readings where Algorithm 1 is silent or literally inconsistent:
     highest index) sets gateDelay, read in row 2*(new pin value) + (new y)
     and in the column of the other pins' values after the switch.
 
+PATHPULSEPERCENT (Section 3: Algorithm 1 assumes 100, and other values edit
+the output test).  ``pulse_gate`` = pct turns the output test into
+100 (t_o - allW[p_o]) < pct gateDelay; ``pulse_wire`` = pct turns the
+interconnect test into 100 (allW[p_i+2] - allW[p_i+1]) < pct netDelay.
+Below 100 a pulse can be shorter than the delay difference of its two
+edges, so both tests also drop a pulse whose width after the delays is
+zero or negative (at 100 that case is already covered).  0 is transport
+delay.
+
 Pure Python: use it on small cases only.
 """
 from __future__ import annotations
@@ -48,7 +57,8 @@ def _without_bit(col: int, i: int) -> int:
     return (col & ((1 << i) - 1)) | ((col >> (i + 1)) << i)
 
 
-def resimulate_gate(allW_in: list, n: int, Y: int, delta: list, d: list) -> list:
+def resimulate_gate(allW_in: list, n: int, Y: int, delta: list, d: list,
+                    pulse_gate: int = 100, pulse_wire: int = 100) -> list:
     """Algorithm 1 for one gate and one window.
 
     allW_in  -- per pin i (0-based; the paper's pin i+1) the input waveform
@@ -79,7 +89,14 @@ def resimulate_gate(allW_in: list, n: int, Y: int, delta: list, d: list) -> list
         for i in range(n):
             W = allW_in[i]
             netDelay = delta[i][1] if p[i] % 2 else delta[i][0]
-            while W[p[i] + 1] != EOW and W[p[i] + 2] - netDelay - W[p[i] + 1] < 0:
+            while W[p[i] + 1] != EOW and W[p[i] + 2] != EOW:
+                # the pulse (p_i+1, p_i+2): its second edge has the other
+                # direction, so the other delay
+                nextDelay = delta[i][0] if p[i] % 2 else delta[i][1]
+                narrow = 100 * (W[p[i] + 2] - W[p[i] + 1]) < pulse_wire * netDelay
+                crossed = W[p[i] + 2] + nextDelay <= W[p[i] + 1] + netDelay
+                if not (narrow or crossed):
+                    break
                 p[i] += 2
             if W[p[i] + 1] != EOW:
                 t_i = min(t_i, W[p[i] + 1] + netDelay)
@@ -95,7 +112,7 @@ def resimulate_gate(allW_in: list, n: int, Y: int, delta: list, d: list) -> list
                     gateDelay = d[i][(2 * (p[i] % 2) + y) * 8 + _without_bit(colInd, i)]
             if y != p_o % 2:
                 t_o = t_i + gateDelay
-                if t_o - out[p_o] < gateDelay:
+                if 100 * (t_o - out[p_o]) < pulse_gate * gateDelay or t_o <= out[p_o]:
                     p_o -= 1                       # cancel the last kept edge
                 else:
                     p_o += 1
@@ -106,7 +123,8 @@ def resimulate_gate(allW_in: list, n: int, Y: int, delta: list, d: list) -> list
     return out[:p_o + 1] + [EOW]
 
 
-def simulate_window(netlist, delays, stim, w: int, W: int = 1):
+def simulate_window(netlist, delays, stim, w: int, W: int = 1, pulse_gate: int = 100,
+                    pulse_wire: int = 100):
     """All nets of window w: returns a list of (init, times) per net id.
 
     Inputs of window w start from their value after the cycles before the
@@ -131,7 +149,7 @@ def simulate_window(netlist, delays, stim, w: int, W: int = 1):
         ins = [waves[int(netlist.fanin_net[q])] for q in range(a, b)]
         delta = [(int(delays.wire_delay[2 * q]), int(delays.wire_delay[2 * q + 1])) for q in range(a, b)]
         d = [[int(v) for v in delays.gate_delay[32 * q:32 * q + 32]] for q in range(a, b)]
-        waves.append(resimulate_gate(ins, n, int(netlist.lut[g]), delta, d))
+        waves.append(resimulate_gate(ins, n, int(netlist.lut[g]), delta, d, pulse_gate, pulse_wire))
     return [from_array(x) for x in waves]
 
 

@@ -23,6 +23,9 @@
  *   - gate inertial filtering with PATHPULSEPERCENT = 100: a new output edge
  *     closer than gateDelay to the last kept output edge cancels that edge
  *     instead of being added (Algorithm 1, output update; Section 3 text).
+ *     Other PATHPULSEPERCENT values replace gateDelay in that test by
+ *     percent/100 of it, as Section 3 says they may; the same percentage may
+ *     be set for the interconnect test (osim_set_pulse, default 100/100).
  *
  * The simulator is structured unlike the level-by-level sweep of the paper:
  * every window is simulated with one global event queue ordered by time.
@@ -36,6 +39,21 @@
  *   gate:  the paper cancels the last kept output edge E when
  *          t_o - E < gateDelay with t_o = t + gateDelay, i.e. when E > t:
  *          E has not happened yet.  Equality keeps both edges.
+ *
+ * With a pulse limit of pct percent (0..100) the tests read
+ *   wire:  drop the pair when 100 (t_{j+1} - t_j) < pct delta(e_j), or when
+ *          the second edge's delayed arrival would not come after the
+ *          first's (a pulse of zero or negative width after the delay);
+ *   gate:  cancel E when 100 (t_o - E) < pct gateDelay, or t_o <= E.
+ * Either test can only hit an arrival or output edge that is still in the
+ * future (the limit never exceeds the delay), so both stay causal.  Below
+ * 100 percent several of a pin's arrivals, or of a gate's kept output
+ * edges, can be in flight at once: the wire test always concerns the pin's
+ * latest edge (and after a drop the next edge is not tested, as the pair
+ * scan of Algorithm 1 restarts behind the dropped pair), while the gate test
+ * concerns the last kept output edge, and a cancel exposes the one kept
+ * before it (a stack: the output pointer moves back by one).  At 100 percent
+ * this reduces to the rules above.
  *
  * Readings of points the paper leaves open (each is listed in the design
  * notes of the repository):
@@ -74,13 +92,16 @@ enum {
   M_WINDOW_INIT_FROM_CYCLE0 = 8,
   M_NO_WIRE_FILTER = 9,
   M_NO_GATE_FILTER = 10,
-  M_OUT_DELAY_FROM_OLD_Y = 11
+  M_OUT_DELAY_FROM_OLD_Y = 11,
+  M_GATE_STACK_DEPTH_ONE = 12,
+  M_WIRE_CROSSING_KEPT = 13
 };
 
 typedef struct { uint64_t key; int64_t seq; } event_t;
 
 typedef struct {
   int32_t I, G, N, P, C, L, W, mutation;
+  int32_t pulse_gate, pulse_wire;  /* pulse limits, percent of the delay */
   const int32_t *fanin_ptr, *fanin_net, *gate_delay, *wire_delay, *edge_time;
   const uint16_t* lut;
   const uint8_t* init;
@@ -89,10 +110,13 @@ typedef struct {
   /* window state */
   uint8_t *netval, *pinval, *vs;
   int32_t *arr_time, *last_time;
+  int32_t *arr_src, *arr_delay;   /* latest kept edge of each pin: its time, its delay */
   int64_t *arr_seq, *last_seq;
   event_t* heap;
   int64_t heap_n, heap_cap;
-  uint8_t* cancelled;
+  uint8_t* cancelled;   /* per event: 1 cancelled, 2 fired (output edges) */
+  int64_t* below;       /* per output-edge event: the gate's kept edge before it */
+  int32_t* seq_time;    /* per event: its time */
   int64_t seq_n, seq_cap;
   int32_t *log_net, *log_time;
   int64_t log_n, log_cap;
@@ -161,9 +185,22 @@ static event_t heap_pop(osim_t* s) {
   return top;
 }
 
-static int64_t new_seq(osim_t* s) {
-  if (grow((void**)&s->cancelled, &s->seq_cap, s->seq_n + 1, 1)) return -1;
+static int64_t new_seq(osim_t* s, int32_t t) {
+  if (s->seq_n + 1 > s->seq_cap) {
+    int64_t cap = s->seq_cap;
+    if (grow((void**)&s->cancelled, &cap, s->seq_n + 1, 1)) return -1;
+    /* the other per-event arrays grow in lockstep */
+    void* a = realloc(s->below, sizeof(int64_t) * (size_t)cap);
+    if (!a) return -1;
+    s->below = (int64_t*)a;
+    void* b = realloc(s->seq_time, sizeof(int32_t) * (size_t)cap);
+    if (!b) return -1;
+    s->seq_time = (int32_t*)b;
+    s->seq_cap = cap;
+  }
   s->cancelled[s->seq_n] = 0;
+  s->below[s->seq_n] = NONE;
+  s->seq_time[s->seq_n] = t;
   return s->seq_n++;
 }
 
@@ -172,7 +209,9 @@ API void osim_destroy(osim_t* s) {
   free(s->gate_of_pin); free(s->fo_ptr); free(s->fo_pin);
   free(s->netval); free(s->pinval); free(s->vs);
   free(s->arr_time); free(s->last_time); free(s->arr_seq); free(s->last_seq);
-  free(s->heap); free(s->cancelled); free(s->log_net); free(s->log_time);
+  free(s->arr_src); free(s->arr_delay);
+  free(s->heap); free(s->cancelled); free(s->below); free(s->seq_time);
+  free(s->log_net); free(s->log_time);
   free(s->res_init); free(s->res_ptr); free(s->res_times); free(s->res_t1);
   free(s);
 }
@@ -196,6 +235,8 @@ API osim_t* osim_create(int32_t I, int32_t G, const int32_t* fanin_ptr,
   if (!s) return NULL;
   s->I = I; s->G = G; s->N = I + G; s->C = C; s->L = L; s->W = W;
   s->mutation = mutation;
+  s->pulse_gate = 100;
+  s->pulse_wire = 100;
   s->fanin_ptr = fanin_ptr; s->fanin_net = fanin_net; s->lut = lut;
   s->gate_delay = gate_delay; s->wire_delay = wire_delay;
   s->init = init; s->edge_ptr = edge_ptr; s->edge_time = edge_time;
@@ -209,13 +250,15 @@ API osim_t* osim_create(int32_t I, int32_t G, const int32_t* fanin_ptr,
   s->vs = (uint8_t*)malloc((size_t)G + 1);
   s->arr_time = (int32_t*)malloc(sizeof(int32_t) * (size_t)(P + 1));
   s->arr_seq = (int64_t*)malloc(sizeof(int64_t) * (size_t)(P + 1));
+  s->arr_src = (int32_t*)malloc(sizeof(int32_t) * (size_t)(P + 1));
+  s->arr_delay = (int32_t*)malloc(sizeof(int32_t) * (size_t)(P + 1));
   s->last_time = (int32_t*)malloc(sizeof(int32_t) * (size_t)(G + 1));
   s->last_seq = (int64_t*)malloc(sizeof(int64_t) * (size_t)(G + 1));
   s->res_init = (uint8_t*)malloc((size_t)N + 1);
   s->res_ptr = (int64_t*)malloc(sizeof(int64_t) * (size_t)(N + 1));
   s->res_t1 = (int64_t*)malloc(sizeof(int64_t) * (size_t)(N + 1));
   if (!s->gate_of_pin || !s->fo_ptr || !s->fo_pin || !s->netval || !s->pinval ||
-      !s->vs || !s->arr_time || !s->arr_seq || !s->last_time || !s->last_seq ||
+      !s->vs || !s->arr_time || !s->arr_seq || !s->arr_src || !s->arr_delay || !s->last_time || !s->last_seq ||
       !s->res_init || !s->res_ptr || !s->res_t1) {
     osim_destroy(s);
     return NULL;
@@ -237,6 +280,19 @@ API osim_t* osim_create(int32_t I, int32_t G, const int32_t* fanin_ptr,
   free(fill);
   s->res_window = -1;
   return s;
+}
+
+/*
+ * Pulse limits (PATHPULSEPERCENT) of the gate and interconnect inertial
+ * tests, each 0..100 percent of the delay (100 = Algorithm 1 as printed;
+ * 0 = transport delay, where only pulses of zero or negative width after
+ * the delay vanish).  Returns 0, or -1 for a value out of range.
+ */
+API int32_t osim_set_pulse(osim_t* s, int32_t gate_percent, int32_t wire_percent) {
+  if (gate_percent < 0 || gate_percent > 100 || wire_percent < 0 || wire_percent > 100) return -1;
+  s->pulse_gate = gate_percent;
+  s->pulse_wire = wire_percent;
+  return 0;
 }
 
 API int32_t osim_num_windows(const osim_t* s) {
@@ -280,20 +336,33 @@ static int net_edge(osim_t* s, int32_t n, int32_t t) {
     int use_rise = rising;
     if (s->mutation == M_WIRE_RISE_FALL_SWAPPED) use_rise = !rising;
     int32_t delta = use_rise ? s->wire_delay[2 * p] : s->wire_delay[2 * p + 1];
+    /* the pin's latest edge was kept and its arrival is still ahead */
     int pending = s->arr_seq[p] != NONE &&
                   (s->mutation == M_WIRE_CANCEL_ON_EQUAL ? s->arr_time[p] >= t
                                                          : s->arr_time[p] > t);
     if (s->mutation == M_NO_WIRE_FILTER) pending = 0;
+    int drop = 0;
     if (pending) {
-      /* the earlier edge's arrival has not happened yet: the pulse
-         (earlier edge, this edge) is narrower than its delay and vanishes */
+      /* the pulse (latest edge, this edge) is narrower than the limit, or
+         would arrive with zero or negative width; at 100 percent every
+         pending arrival qualifies, since pending means t - t_prev < delta */
+      int64_t width = (int64_t)t - s->arr_src[p];
+      int crossed = (int64_t)t + delta <= s->arr_time[p] && s->mutation != M_WIRE_CROSSING_KEPT;
+      drop = 100 * width < (int64_t)s->pulse_wire * s->arr_delay[p] || crossed ||
+             s->mutation == M_WIRE_CANCEL_ON_EQUAL;
+    }
+    if (drop) {
+      /* the pulse vanishes: cancel the earlier edge's arrival, schedule
+         nothing, and leave the next edge untested */
       s->cancelled[s->arr_seq[p]] = 1;
       s->arr_seq[p] = NONE;
     } else {
-      int64_t q = new_seq(s);
+      int64_t q = new_seq(s, t + delta);
       if (q < 0 || heap_push(s, t + delta, K_ARRIVAL, p, q)) return -1;
       s->arr_seq[p] = q;
       s->arr_time[p] = t + delta;
+      s->arr_src[p] = t;
+      s->arr_delay[p] = delta;
     }
   }
   return 0;
@@ -304,25 +373,41 @@ static int gate_eval(osim_t* s, int32_t g, int32_t t, int istar, uint32_t col_be
   uint32_t col = col_index(s, g);
   int y = (s->lut[g] >> col) & 1;
   if (y == s->vs[g]) return 0;
-  int pending = s->last_seq[g] != NONE &&
-                (s->mutation == M_GATE_CANCEL_ON_EQUAL ? s->last_time[g] >= t
-                                                       : s->last_time[g] > t);
-  if (s->mutation == M_NO_GATE_FILTER) pending = 0;
-  if (pending) {
-    /* the new edge would come less than gateDelay after the last kept one,
-       which therefore has not happened yet: cancel it */
-    s->cancelled[s->last_seq[g]] = 1;
-    s->last_seq[g] = NONE;
+  /* delay of the new output edge: the switching pin's arc */
+  int32_t p = s->fanin_ptr[g] + istar;
+  int in_edge = s->pinval[p];
+  int out_edge = y;
+  if (s->mutation == M_OUT_DELAY_FROM_OLD_Y) out_edge = s->vs[g];
+  uint32_t side = side_column(s->mutation == M_SIDE_BEFORE_SWITCH ? col_before : col, istar);
+  int row = s->mutation == M_ROW_TRANSPOSED ? (2 * out_edge + in_edge) : (2 * in_edge + out_edge);
+  int32_t d = s->gate_delay[(int64_t)p * 32 + row * 8 + side];
+  int64_t top = s->last_seq[g];
+  int cancel = 0;
+  if (top != NONE) {
+    /* the last kept output edge E is still ahead (kept edges that fired
+       have left the stack) */
+    int64_t E = s->last_time[g];
+    int64_t to = (int64_t)t + d;
+    cancel = 100 * (to - E) < (int64_t)s->pulse_gate * d || to <= E;
+    if (s->mutation == M_GATE_CANCEL_ON_EQUAL) cancel = E >= t;
+  }
+  if (s->mutation == M_NO_GATE_FILTER) cancel = 0;
+  if (cancel) {
+    /* the new edge would come too soon after E: cancel E instead, and the
+       kept edge before it (if still ahead) becomes the last kept one */
+    s->cancelled[top] = 1;
+    int64_t b = s->below[top];
+    if (s->mutation == M_GATE_STACK_DEPTH_ONE) b = NONE;
+    if (b != NONE && s->cancelled[b] == 0) {
+      s->last_seq[g] = b;
+      s->last_time[g] = s->seq_time[b];
+    } else {
+      s->last_seq[g] = NONE;
+    }
   } else {
-    int32_t p = s->fanin_ptr[g] + istar;
-    int in_edge = s->pinval[p];
-    int out_edge = y;
-    if (s->mutation == M_OUT_DELAY_FROM_OLD_Y) out_edge = s->vs[g];
-    uint32_t side = side_column(s->mutation == M_SIDE_BEFORE_SWITCH ? col_before : col, istar);
-    int row = s->mutation == M_ROW_TRANSPOSED ? (2 * out_edge + in_edge) : (2 * in_edge + out_edge);
-    int32_t d = s->gate_delay[(int64_t)p * 32 + row * 8 + side];
-    int64_t q = new_seq(s);
+    int64_t q = new_seq(s, t + d);
     if (q < 0 || heap_push(s, t + d, K_NETEDGE, s->I + g, q)) return -1;
+    s->below[q] = top;
     s->last_seq[g] = q;
     s->last_time[g] = t + d;
   }
@@ -364,8 +449,9 @@ API int64_t osim_run_window(osim_t* s, int32_t w) {
     for (int32_t c = c0; c < c1; ++c) {
       int64_t a = s->edge_ptr[(int64_t)i * s->C + c], b = s->edge_ptr[(int64_t)i * s->C + c + 1];
       for (int64_t e = a; e < b; ++e) {
-        int64_t q = new_seq(s);
-        if (q < 0 || heap_push(s, (c - c0) * s->L + s->edge_time[e], K_NETEDGE, i, q)) return -1;
+        int32_t te = (c - c0) * s->L + s->edge_time[e];
+        int64_t q = new_seq(s, te);
+        if (q < 0 || heap_push(s, te, K_NETEDGE, i, q)) return -1;
       }
     }
   /* event loop: at equal times arrivals come before net edges (key order) */
@@ -376,6 +462,9 @@ API int64_t osim_run_window(osim_t* s, int32_t w) {
     int kind = kind_bit(s, (int)((e.key >> 32) & 1));
     int32_t id = (int32_t)(e.key & 0xffffffffu);
     if (kind == K_NETEDGE) {
+      /* a gate's output edge fires: it is the oldest of its kept edges
+         still ahead, so it leaves the bottom of the gate's stack */
+      s->cancelled[e.seq] = 2;
       if (id >= I && s->last_seq[id - I] == e.seq) s->last_seq[id - I] = NONE;
       if (net_edge(s, id, t)) return -1;
       continue;
@@ -391,7 +480,7 @@ API int64_t osim_run_window(osim_t* s, int32_t w) {
       if (!s->cancelled[cur.seq]) {
         int i = p - s->fanin_ptr[g];
         s->pinval[p] ^= 1;
-        s->arr_seq[p] = NONE;
+        if (s->arr_seq[p] == cur.seq) s->arr_seq[p] = NONE;
         if (i > istar) istar = i;
         if (i < ilow) ilow = i;
       }

@@ -13,7 +13,12 @@ fix, not against the oracle itself.
 * the event-driven simulator and the Algorithm 1 formulation agree on
   thousands of random tiny circuits;
 * every planted mistake in the event simulator is caught by the pins above
-  (not counting the cross-check).
+  (not counting the cross-check);
+* pulse limits other than 100 percent (PATHPULSEPERCENT, Section 3): the
+  hand-traced cases that carry a 'pulse' entry, settled values and
+  invariants at several limits, a transport-delay chain whose narrow pulses
+  all pass shifted by the path delay (closed form), and the two
+  formulations agreeing on random circuits at random limits.
 """
 import numpy as np
 import pytest
@@ -26,8 +31,14 @@ from cases import case_workload, load_hand_traced
 CASES = load_hand_traced()
 
 
-def _event_windows(wl, W, mutation="none"):
-    sim = oracle.EventSim(wl.netlist, wl.delays, wl.stim, W=W, mutation=mutation)
+def _pulse(case):
+    p = case.get("pulse", {})
+    return p.get("gate", 100), p.get("wire", 100)
+
+
+def _event_windows(wl, W, mutation="none", pulse=(100, 100)):
+    sim = oracle.EventSim(wl.netlist, wl.delays, wl.stim, W=W, mutation=mutation,
+                          pulse_gate=pulse[0], pulse_wire=pulse[1])
     out = []
     for w in range(sim.num_windows):
         out.append(oracle.windows_as_lists(*sim.window(w)))
@@ -36,7 +47,7 @@ def _event_windows(wl, W, mutation="none"):
 
 def _golden_failures(case, mutation="none"):
     wl = case_workload(case)
-    sim, wins = _event_windows(wl, case["W"], mutation)
+    sim, wins = _event_windows(wl, case["W"], mutation, _pulse(case))
     fails = []
     for e in case["expect"]:
         got = wins[e["window"]][e["net"]]
@@ -60,7 +71,8 @@ def test_hand_traced_algo1(case):
     wl = case_workload(case)
     W = case["W"]
     nwin = (wl.stim.num_cycles + W - 1) // W
-    wins = [algo1.simulate_window(wl.netlist, wl.delays, wl.stim, w, W) for w in range(nwin)]
+    pg, pw = _pulse(case)
+    wins = [algo1.simulate_window(wl.netlist, wl.delays, wl.stim, w, W, pg, pw) for w in range(nwin)]
     for e in case["expect"]:
         init, times = wins[e["window"]][e["net"]]
         assert (init, list(times)) == (e["init"], e["times"])
@@ -95,8 +107,9 @@ def _zero_delay(netlist, inputs):
     return np.asarray(vals, np.uint8)
 
 
-def _settled_failures(wl, W, mutation="none", windows=None):
-    sim = oracle.EventSim(wl.netlist, wl.delays, wl.stim, W=W, mutation=mutation)
+def _settled_failures(wl, W, mutation="none", windows=None, pulse=(100, 100)):
+    sim = oracle.EventSim(wl.netlist, wl.delays, wl.stim, W=W, mutation=mutation,
+                          pulse_gate=pulse[0], pulse_wire=pulse[1])
     fails = []
     for w in (windows if windows is not None else range(sim.num_windows)):
         init, ptr, times = sim.window(w)
@@ -128,8 +141,9 @@ def test_settled_values(name, kw, W):
 
 # ------------------------------------------------------------- invariants
 
-def _invariant_failures(wl, W, mutation="none"):
-    sim = oracle.EventSim(wl.netlist, wl.delays, wl.stim, W=W, mutation=mutation)
+def _invariant_failures(wl, W, mutation="none", pulse=(100, 100)):
+    sim = oracle.EventSim(wl.netlist, wl.delays, wl.stim, W=W, mutation=mutation,
+                          pulse_gate=pulse[0], pulse_wire=pulse[1])
     fails = []
     I = wl.netlist.num_inputs
     inits, finals = [], []
@@ -162,6 +176,20 @@ def _invariant_failures(wl, W, mutation="none"):
 def test_invariants(W):
     wl = gen.make_workload("tiny", seed=11, num_cycles=12)
     assert _invariant_failures(wl, W) == []
+
+
+PULSES = [(0, 0), (0, 100), (100, 0), (50, 50), (30, 80)]
+
+
+@pytest.mark.parametrize("pulse", PULSES, ids=[f"g{a}w{b}" for a, b in PULSES])
+def test_settled_values_and_invariants_at_pulse_limits(pulse):
+    # a cancel removes one output edge and a dropped wire pulse two input
+    # edges, so the settled values never depend on the limits
+    wl = gen.make_workload("tiny", seed=13, num_cycles=10)
+    assert _settled_failures(wl, 1, pulse=pulse) == []
+    assert _invariant_failures(wl, 2, pulse=pulse) == []
+    wl = gen.make_workload("mid", seed=13, num_cycles=3, num_gates=2000, depth=25, num_inputs=48)
+    assert _settled_failures(wl, 1, pulse=pulse) == []
 
 
 # ------------------------------------------------------------- closed forms
@@ -212,6 +240,43 @@ def test_chain_shift_closed_form(seed):
         assert times[ptr[net]:ptr[net + 1]].tolist() == [t for t, _ in cur]
 
 
+@pytest.mark.parametrize("seed", range(4))
+def test_transport_chain_passes_narrow_pulses_shifted(seed):
+    # equal rise and fall delays at every stage keep every pulse's width, so
+    # with both limits at 0 (transport) each input edge comes out shifted by
+    # the sum of the path's delays, however narrow its pulse; at 100 percent
+    # the same pulses (narrower than every delay) all vanish
+    depth = 4 + 3 * seed
+    rng = np.random.Generator(np.random.PCG64(500 + seed))
+    inv = rng.integers(0, 2, depth)
+    lut = np.where(inv == 1, gen.cell_lut("INV"), gen.cell_lut("BUF")).astype(np.uint16)
+    w = rng.integers(10, 30, depth)
+    g = rng.integers(10, 50, depth)
+    wire = np.stack([w, w], 1).astype(np.int32)
+    gd = np.zeros((depth, 2, 2, 8), np.int32)
+    gd[:, :, :, 0] = g[:, None, None]
+    nl = gen.Netlist(1, np.arange(depth + 1, dtype=np.int32), np.arange(depth, dtype=np.int32),
+                     np.ones(depth, np.uint8), lut, np.zeros(depth, np.uint8))
+    dl = gen.Delays(gd.reshape(-1), wire.reshape(-1))
+    starts = np.arange(1, 6) * 150 + rng.integers(0, 20, 5)
+    widths = rng.integers(1, 10, 5)
+    t_in = np.sort(np.concatenate([starts, starts + widths])).astype(np.int32)
+    init0 = int(rng.integers(0, 2))
+    st = gen.Stimulus(1, 4000, np.asarray([init0], np.uint8), np.asarray([0, t_in.size], np.int64), t_in)
+    init, ptr, times = oracle.EventSim(nl, dl, st, W=1, pulse_gate=0, pulse_wire=0).window(0)
+    shift = np.cumsum(w + g)
+    v = init0
+    for j in range(depth):
+        v ^= int(inv[j])
+        net = 1 + j
+        assert int(init[net]) == v
+        assert times[ptr[net]:ptr[net + 1]].tolist() == (t_in + shift[j]).tolist()
+    a1 = algo1.simulate_window(nl, dl, st, 0, 1, 0, 0)
+    assert [list(t) for _, t in a1[1:]] == [times[ptr[n]:ptr[n + 1]].tolist() for n in range(1, depth + 1)]
+    _, ptr100, _ = oracle.EventSim(nl, dl, st, W=1).window(0)
+    assert np.all(np.diff(ptr100)[1:] == 0)
+
+
 def test_narrow_pulses_never_pass():
     wl = gen.make_workload("tiny", seed=5, num_cycles=10)
     # every input pulse narrower than every wire delay (>= 3 here)
@@ -242,6 +307,20 @@ def test_event_sim_matches_algorithm1_random(block):
             ev = oracle.windows_as_lists(*sim.window(w))
             a1 = [(i, list(t)) for i, t in algo1.simulate_window(wl.netlist, wl.delays, wl.stim, w, W)]
             assert ev == a1, f"random case {s} window {w}"
+
+
+@pytest.mark.parametrize("block", range(2))
+def test_event_sim_matches_algorithm1_random_pulse_limits(block):
+    rng = np.random.Generator(np.random.PCG64(77 + block))
+    for s in range(5000 + block * 400, 5000 + block * 400 + 400):
+        wl = gen.random_small(s)
+        W = 1 + s % 2
+        pg, pw = (int(x) for x in rng.choice([0, 1, 25, 50, 99, 100], 2))
+        sim = oracle.EventSim(wl.netlist, wl.delays, wl.stim, W=W, pulse_gate=pg, pulse_wire=pw)
+        for w in range(sim.num_windows):
+            ev = oracle.windows_as_lists(*sim.window(w))
+            a1 = [(i, list(t)) for i, t in algo1.simulate_window(wl.netlist, wl.delays, wl.stim, w, W, pg, pw)]
+            assert ev == a1, f"random case {s} window {w} limits {pg}/{pw}"
 
 
 def test_event_sim_matches_algorithm1_recipes():
