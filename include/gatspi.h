@@ -16,7 +16,8 @@
  *     time switch before the output is re-evaluated);
  *   - gate delays read from the switching pin's table, indexed by its edge,
  *     the output edge and the other pins' values (SDF COND);
- *   - gate inertial filtering with PATHPULSEPERCENT = 100;
+ *   - gate inertial filtering with PATHPULSEPERCENT = 100 (or other pulse
+ *     limits for the gate and interconnect tests, gatspi_opts);
  * and every net is reduced to SAIF figures T0 / T1 / TC (Section 3: the
  * simulator produces SAIF files for power analysis).
  *
@@ -79,7 +80,22 @@ typedef struct gatspi_opts {
                                0 = autotuned (see tile_items) or 4 */
   int32_t digest;        /* 1 = also reduce every (net, window) waveform to a
                             per-net 64-bit digest (gatspi_digest) */
-  int32_t reserved[2];   /* must be 0 */
+  int32_t pulse_limits;  /* 1 = the two pulse limits below apply; 0 = both
+                            100 percent (Algorithm 1 as printed) */
+  int32_t gate_pulse_percent; /* PATHPULSEPERCENT of the gate inertial test
+                            (Section 3: Algorithm 1 assumes 100 and other
+                            values edit its output test), 0..100: the last
+                            kept output edge E is cancelled when
+                            100 (t_o - E) < percent * gateDelay or t_o <= E;
+                            0 is transport delay */
+  int32_t wire_pulse_percent; /* the same for the interconnect test, 0..100:
+                            a pulse (t_j, t_j+1) on a pin is dropped when
+                            100 (t_j+1 - t_j) < percent * delta(e_j), or when
+                            its delayed edges would not stay in order.  With
+                            pulse limits the launch shape is 256 threads x 4
+                            windows unless tile_items / items_per_thread ask
+                            for 256 x 1, 256 x 2 or 128 x 8 (no autotuning) */
+  int32_t reserved;      /* must be 0 */
 } gatspi_opts;
 
 /* Figures of the last gatspi_simulate call. */
@@ -182,6 +198,39 @@ int gatspi_set_stimulus(gatspi_ctx* ctx, int32_t num_cycles, int32_t cycle_ps,
  * ECAPACITY, ETIMEOUT, ECUDA.
  */
 int gatspi_simulate(gatspi_ctx* ctx, const gatspi_opts* opts);
+
+/* What gatspi_resimulate_edit did. */
+typedef struct gatspi_resim_info {
+  int32_t mode;        /* 0: no gate's delays changed, nothing ran; 1: only
+                          the fanout cone of the changed gates ran; 2: the
+                          whole simulation ran again */
+  int32_t cone_gates;  /* gates simulated again */
+  int32_t first_level; /* lowest level simulated again (0 with mode 0) */
+  int32_t levels;      /* levels with a launch */
+  int64_t items;       /* (gate, window) items simulated again */
+} gatspi_resim_info;
+
+/*
+ * Set a delay edit (same arrays and rules as gatspi_set_edit; it replaces
+ * the current edit) and bring the last simulation's results up to date --
+ * the glitch-optimization loop of Section 4: re-simulate, resize cells,
+ * re-simulate.  Only gates whose delays change, and the gates in their
+ * fanout cone, can get new waveforms, so when the last gatspi_simulate kept
+ * every window in one resident batch (with at least 64 windows: gate-aligned
+ * tiles) and nothing else was loaded since, only the cone is simulated again,
+ * level by level, reading the other gates' waveforms where they are; the
+ * cone's new waveforms go to free arena space after everything stored, and
+ * its nets' SAIF (and digest, if the last run made one) is recomputed.
+ * Otherwise -- several batches, a stimulus, netlist or delay load since, or
+ * too little free arena for the cone -- it runs gatspi_simulate again with the
+ * last call's options.  Either way, SAIF, digest and resident waveforms are
+ * those of a full gatspi_simulate with the new edit.  Synchronous.
+ * gatspi_get_stats afterwards describes the cone's launches (mode 1).
+ * `info` may be NULL.  Errors: ESTATE (nothing simulated), EINVAL (edits),
+ * and those of gatspi_simulate.
+ */
+int gatspi_resimulate_edit(gatspi_ctx* ctx, int32_t n_edits, const int32_t* edit_gate,
+                           const int32_t* edit_delta, gatspi_resim_info* info);
 
 /*
  * SAIF of the last simulation, per net in the caller's net numbering:

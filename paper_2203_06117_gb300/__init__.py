@@ -45,7 +45,7 @@ EXPORTS = ["gatspi_create", "gatspi_destroy", "gatspi_last_error", "gatspi_load_
            "gatspi_engine_create", "gatspi_engine_destroy", "gatspi_engine_last_error",
            "gatspi_engine_add_netlist", "gatspi_engine_submit", "gatspi_engine_step",
            "gatspi_engine_drain", "gatspi_engine_poll", "gatspi_engine_release",
-           "gatspi_engine_get_stats", "gatspi_propagate_level_noalloc"]
+           "gatspi_engine_get_stats", "gatspi_propagate_level_noalloc", "gatspi_resimulate_edit"]
 
 JOB_QUEUED, JOB_RUNNING, JOB_DONE, JOB_FAILED = 0, 1, 2, 3
 
@@ -82,7 +82,8 @@ class gatspi_opts(ctypes.Structure):
     _fields_ = [("window_cycles", ctypes.c_int32), ("batch_windows", ctypes.c_int32),
                 ("tile_items", ctypes.c_int32), ("time_kernels", ctypes.c_int32),
                 ("items_per_thread", ctypes.c_int32), ("digest", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 2)]
+                ("pulse_limits", ctypes.c_int32), ("gate_pulse_percent", ctypes.c_int32),
+                ("wire_pulse_percent", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class gatspi_engine_opts(ctypes.Structure):
@@ -113,6 +114,15 @@ class gatspi_level_args(ctypes.Structure):
                                                "num_windows", "first_window", "window_cycles",
                                                "num_cycles", "cycle_ps", "err_len")] + \
                [("err", ctypes.c_char_p)]
+
+
+class gatspi_resim_info(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int32), ("cone_gates", ctypes.c_int32),
+                ("first_level", ctypes.c_int32), ("levels", ctypes.c_int32),
+                ("items", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class gatspi_stats(ctypes.Structure):
@@ -149,6 +159,7 @@ def lib():
         L.gatspi_load_delays.argtypes = [vp, vp, vp]
         L.gatspi_set_stimulus.argtypes = [vp, i32, i32, vp, vp, vp]
         L.gatspi_set_edit.argtypes = [vp, i32, vp, vp]
+        L.gatspi_resimulate_edit.argtypes = [vp, i32, vp, vp, ctypes.POINTER(gatspi_resim_info)]
         L.gatspi_simulate.argtypes = [vp, ctypes.POINTER(gatspi_opts)]
         L.gatspi_saif.argtypes = [vp, vp, vp, vp]
         L.gatspi_read_window.argtypes = [vp, i32, vp, vp, vp, i64, ctypes.POINTER(ctypes.c_int64)]
@@ -223,6 +234,19 @@ def gatspi_set_edit(ctx, edit_gate=None, edit_delta=None) -> None:
     _check(ctx, lib().gatspi_set_edit(ctx, n, _ptr(eg), _ptr(ed)))
 
 
+def gatspi_resimulate_edit(ctx, edit_gate=None, edit_delta=None) -> dict:
+    """Set a delay edit and bring the last simulation up to date (only the
+    fanout cone of the changed gates runs when the result is resident).
+    Returns the call's gatspi_resim_info as a dict (mode 0: nothing changed,
+    1: cone only, 2: everything again)."""
+    n = 0 if edit_gate is None else len(edit_gate)
+    eg = None if n == 0 else _arr(edit_gate, np.int32)
+    ed = None if n == 0 else _arr(edit_delta, np.int32)
+    info = gatspi_resim_info()
+    _check(ctx, lib().gatspi_resimulate_edit(ctx, n, _ptr(eg), _ptr(ed), ctypes.byref(info)))
+    return info.as_dict()
+
+
 def gatspi_set_stimulus(ctx, num_cycles, cycle_ps, init, edge_ptr, edge_time) -> None:
     iv, ep, et = _arr(init, np.uint8), _arr(edge_ptr, np.int64), _arr(edge_time, np.int32)
     _check(ctx, lib().gatspi_set_stimulus(ctx, int(num_cycles), int(cycle_ps), _ptr(iv), _ptr(ep),
@@ -230,9 +254,12 @@ def gatspi_set_stimulus(ctx, num_cycles, cycle_ps, init, edge_ptr, edge_time) ->
 
 
 def gatspi_simulate(ctx, window_cycles=0, batch_windows=0, tile_items=0, time_kernels=0,
-                    items_per_thread=0, digest=0) -> None:
+                    items_per_thread=0, digest=0, pulse=None) -> None:
+    """``pulse``: None for Algorithm 1 as printed, else (gate percent, wire
+    percent), the PATHPULSEPERCENT limits of the two inertial tests."""
+    pg, pw = pulse if pulse is not None else (100, 100)
     o = gatspi_opts(int(window_cycles), int(batch_windows), int(tile_items), int(time_kernels),
-                    int(items_per_thread), int(digest))
+                    int(items_per_thread), int(digest), 1 if pulse is not None else 0, int(pg), int(pw))
     _check(ctx, lib().gatspi_simulate(ctx, ctypes.byref(o)))
 
 
@@ -294,6 +321,9 @@ class Simulator:
 
     def window(self, w: int):
         return gatspi_read_window(self.ctx, w, self.N)
+
+    def resimulate_edit(self, edit_gate=None, edit_delta=None) -> dict:
+        return gatspi_resimulate_edit(self.ctx, edit_gate, edit_delta)
 
     def digest(self):
         return gatspi_digest(self.ctx, self.N)

@@ -79,6 +79,7 @@ struct gatspi_ctx {
   std::vector<long long> gkey;
   int64_t generation = 0;      // bumped by every load/edit/stimulus call
   int eager_nt = 0, eager_ipt = 0;  // a launch shape already run eagerly
+  bool eager_pp = false;             // ... and whether with pulse limits
   long long* d_in_prefix = nullptr;
   int64_t total_time = 0;
 
@@ -96,6 +97,16 @@ struct gatspi_ctx {
   int32_t* d_times = nullptr;
   int64_t times_cap = 0;
   size_t scratch_bytes = 0;  // counters (zeroed per batch)
+
+  // incremental re-simulation after a delay edit (gatspi_resimulate_edit)
+  gatspi_opts last_opts{};         // options of the last gatspi_simulate, launch shape resolved
+  int64_t result_gen = -1;         // generation the resident result belongs to
+  bool result_single = false;      // the result is one resident batch with gate-aligned tiles
+  int64_t append_ptr = 0;          // first element of times past every stored run
+  std::vector<int32_t> delta;      // delay edit per internal gate (empty: none)
+  std::vector<int32_t> fo_ptr, fo_gate;  // fanout gates per internal net (built on first use)
+  int32_t* d_cone = nullptr;       // cone gate lists, level after level
+  long long* d_append = nullptr;   // two words: where a cone launch starts / the next one starts
 
   // last simulation
   int32_t W = 1, batch_w0 = 0, batch_nw = 0, n_windows = 0, tile = 256;
@@ -136,6 +147,10 @@ int upload(gatspi_ctx* ctx, T*& dst, const T* src, size_t n) {
 void free_netlist(gatspi_ctx* c) {
   dfree(c->d_gate_delta);
   c->max_edit = 0;
+  c->delta.clear();
+  c->fo_ptr.clear();
+  c->fo_gate.clear();
+  dfree(c->d_cone);
   dfree(c->d_fanin_ptr); dfree(c->d_fanin_net); dfree(c->d_net_level); dfree(c->d_lut);
   dfree(c->d_gate_desc);
   dfree(c->d_gate_delay); dfree(c->d_wire_delay); dfree(c->d_t1); dfree(c->d_tc); dfree(c->d_digest);
@@ -221,6 +236,41 @@ size_t fixed_bytes(const gatspi_ctx* c, int32_t NW, int ipt) {
                   align_up((int64_t)(c->D + 2) * 8) + align_up((c->D + 2) * 4) + 4096);
 }
 
+// The edit as one delta per internal gate (all zero: empty vector).
+int edit_vector(gatspi_ctx* ctx, int32_t n_edits, const int32_t* edit_gate, const int32_t* edit_delta,
+                std::vector<int32_t>* out) {
+  if (n_edits < 0 || (n_edits > 0 && (!edit_gate || !edit_delta)))
+    return fail(ctx, GATSPI_EINVAL, "bad delay edit arrays");
+  out->clear();
+  if (n_edits == 0) return GATSPI_OK;
+  std::vector<int32_t> delta(ctx->G, 0);
+  bool any = false;
+  for (int32_t k = 0; k < n_edits; ++k) {
+    const int32_t g = edit_gate[k];
+    if (g < 0 || g >= ctx->G) return fail(ctx, GATSPI_EINVAL, "edit names an unknown gate");
+    if (edit_delta[k] < -gatspi_host::kMaxDelay || edit_delta[k] > gatspi_host::kMaxDelay)
+      return fail(ctx, GATSPI_EINVAL, "edit delta outside +-2^24 ps");
+    delta[ctx->net_int[(size_t)ctx->I + g] - ctx->I] = edit_delta[k];
+    any = any || edit_delta[k] != 0;
+  }
+  if (any) *out = std::move(delta);
+  return GATSPI_OK;
+}
+
+// Make `delta` the current edit (device copy and host copy).
+int apply_edit(gatspi_ctx* ctx, std::vector<int32_t> delta) {
+  CK(cudaSetDevice(ctx->device));
+  dfree(ctx->d_gate_delta);
+  ctx->max_edit = 0;
+  ctx->delta.clear();
+  if (delta.empty()) return GATSPI_OK;
+  int rc;
+  if ((rc = upload(ctx, ctx->d_gate_delta, delta.data(), delta.size()))) return rc;
+  ctx->max_edit = std::max(0, *std::max_element(delta.begin(), delta.end()));
+  ctx->delta = std::move(delta);
+  return GATSPI_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -259,6 +309,7 @@ int gatspi_destroy(gatspi_ctx* ctx) {
   free_stim(ctx);
   free_arena(ctx);
   dfree(ctx->d_status);
+  dfree(ctx->d_append);
   if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
   if (ctx->h_in_prefix) cudaFreeHost(ctx->h_in_prefix);
   if (ctx->h_ret) cudaFreeHost(ctx->h_ret);
@@ -332,6 +383,7 @@ int gatspi_load_delays(gatspi_ctx* ctx, const int32_t* gate_delay, const int32_t
   ctx->max_wire_delay = mw;
   dfree(ctx->d_gate_delta);
   ctx->max_edit = 0;
+  ctx->delta.clear();
   ctx->have_delays = true;
   ctx->have_result = false;
   return GATSPI_OK;
@@ -341,29 +393,11 @@ int gatspi_set_edit(gatspi_ctx* ctx, int32_t n_edits, const int32_t* edit_gate, 
   if (!ctx) return GATSPI_EINVAL;
   ctx->generation++;
   if (!ctx->have_delays) return fail(ctx, GATSPI_ESTATE, "load delays before an edit");
-  if (n_edits < 0 || (n_edits > 0 && (!edit_gate || !edit_delta)))
-    return fail(ctx, GATSPI_EINVAL, "bad delay edit arrays");
-  CK(cudaSetDevice(ctx->device));
+  std::vector<int32_t> delta;
+  int rc = edit_vector(ctx, n_edits, edit_gate, edit_delta, &delta);
+  if (rc) return rc;
   ctx->have_result = false;
-  if (n_edits == 0) {
-    dfree(ctx->d_gate_delta);
-    ctx->max_edit = 0;
-    return GATSPI_OK;
-  }
-  std::vector<int32_t> delta(ctx->G, 0);
-  int32_t mx = 0;
-  for (int32_t k = 0; k < n_edits; ++k) {
-    const int32_t g = edit_gate[k];
-    if (g < 0 || g >= ctx->G) return fail(ctx, GATSPI_EINVAL, "edit names an unknown gate");
-    if (edit_delta[k] < -gatspi_host::kMaxDelay || edit_delta[k] > gatspi_host::kMaxDelay)
-      return fail(ctx, GATSPI_EINVAL, "edit delta outside +-2^24 ps");
-    delta[ctx->net_int[(size_t)ctx->I + g] - ctx->I] = edit_delta[k];
-    mx = std::max(mx, edit_delta[k]);
-  }
-  int rc;
-  if ((rc = upload(ctx, ctx->d_gate_delta, delta.data(), delta.size()))) return rc;
-  ctx->max_edit = mx;
-  return GATSPI_OK;
+  return apply_edit(ctx, std::move(delta));
 }
 
 int gatspi_set_stimulus(gatspi_ctx* ctx, int32_t num_cycles, int32_t cycle_ps, const uint8_t* init,
@@ -394,6 +428,22 @@ int gatspi_set_stimulus(gatspi_ctx* ctx, int32_t num_cycles, int32_t cycle_ps, c
 
 namespace {
 
+// The kernels' view of the loaded job and the carved batch.
+JobView job_view(const gatspi_ctx* ctx, int32_t nw, int32_t w0, int32_t W, int32_t pulse_g, int32_t pulse_w) {
+  JobView job{};
+  job.fanin_ptr = ctx->d_fanin_ptr; job.fanin_net = ctx->d_fanin_net; job.lut = ctx->d_lut;
+  job.gate_delay = ctx->d_gate_delay; job.wire_delay = ctx->d_wire_delay;
+  job.net_level = ctx->d_net_level; job.gate_delta = ctx->d_gate_delta;
+  job.gdesc = (const int4*)ctx->d_gate_desc;
+  job.rstart = ctx->d_rstart; job.tinfo = ctx->d_tinfo; job.T = ctx->batch_T; job.rmeta = ctx->d_rmeta;
+  job.times = ctx->d_times; job.lvl_base = ctx->d_lvl_base;
+  job.capacity = ctx->times_cap; job.saif_t1 = ctx->d_t1; job.saif_tc = ctx->d_tc;
+  job.status = ctx->d_status;
+  job.I = ctx->I; job.NW = nw; job.w0 = w0; job.W = W; job.C = ctx->C; job.L = ctx->L;
+  job.pulse_g = pulse_g; job.pulse_w = pulse_w;
+  return job;
+}
+
 int simulate_impl(gatspi_ctx* ctx, const gatspi_opts* opts) {
   if (!ctx->have_netlist || !ctx->have_delays || !ctx->have_stim)
     return fail(ctx, GATSPI_ESTATE, "load a netlist, its delays and a stimulus first");
@@ -401,9 +451,15 @@ int simulate_impl(gatspi_ctx* ctx, const gatspi_opts* opts) {
   CK(cudaSetDevice(ctx->device));
   gatspi_opts o{};
   if (opts) o = *opts;
-  for (int k = 0; k < 2; ++k)
-    if (o.reserved[k]) return fail(ctx, GATSPI_EINVAL, "reserved option fields must be 0");
+  if (o.reserved) return fail(ctx, GATSPI_EINVAL, "reserved option fields must be 0");
   if (o.digest < 0 || o.digest > 1) return fail(ctx, GATSPI_EINVAL, "digest must be 0 or 1");
+  if (o.pulse_limits < 0 || o.pulse_limits > 1) return fail(ctx, GATSPI_EINVAL, "pulse_limits must be 0 or 1");
+  const int32_t pulse_g = o.pulse_limits ? o.gate_pulse_percent : 100;
+  const int32_t pulse_w = o.pulse_limits ? o.wire_pulse_percent : 100;
+  if (pulse_g < 0 || pulse_g > 100 || pulse_w < 0 || pulse_w > 100)
+    return fail(ctx, GATSPI_EINVAL, "pulse limits must be 0..100 percent");
+  // Algorithm 1 as printed unless a limit is below 100 percent
+  const bool pp = pulse_g != 100 || pulse_w != 100;
   const int32_t W = o.window_cycles ? o.window_cycles : 1;
   if (W < 1) return fail(ctx, GATSPI_EINVAL, "window_cycles must be >= 1");
   const int nt = o.tile_items ? o.tile_items : 256;
@@ -412,6 +468,9 @@ int simulate_impl(gatspi_ctx* ctx, const gatspi_opts* opts) {
       (nt == 512 && ipt == 8))
     return fail(ctx, GATSPI_EINVAL, "tile_items must be 128, 256 or 512 and items_per_thread 1, 2, 4 or 8 "
                                     "(at most 4 with 512)");
+  if (pp && !pulse_variant_compiled(nt, ipt))
+    return fail(ctx, GATSPI_EINVAL, "with pulse limits the launch shape must be 256 x 1, 256 x 2, 256 x 4 "
+                                    "or 128 x 8 (threads x items_per_thread)");
   const int tile = tile_items_of(ipt);  // items per warp tile
   if (o.batch_windows < 0) return fail(ctx, GATSPI_EINVAL, "batch_windows must be >= 0");
   // every time stays below 2^31: window length plus the longest path
@@ -511,16 +570,7 @@ int simulate_impl(gatspi_ctx* ctx, const gatspi_opts* opts) {
         if ((e = cudaGetLastError())) return e;
         if (o.time_kernels && (e = rec(ctx->ev[1]))) return e;
       }
-      JobView job{};
-      job.fanin_ptr = ctx->d_fanin_ptr; job.fanin_net = ctx->d_fanin_net; job.lut = ctx->d_lut;
-      job.gate_delay = ctx->d_gate_delay; job.wire_delay = ctx->d_wire_delay;
-      job.net_level = ctx->d_net_level; job.gate_delta = ctx->d_gate_delta;
-      job.gdesc = (const int4*)ctx->d_gate_desc;
-      job.rstart = ctx->d_rstart; job.tinfo = ctx->d_tinfo; job.T = ctx->batch_T; job.rmeta = ctx->d_rmeta;
-      job.times = ctx->d_times; job.lvl_base = ctx->d_lvl_base;
-      job.capacity = ctx->times_cap; job.saif_t1 = ctx->d_t1; job.saif_tc = ctx->d_tc;
-      job.status = ctx->d_status;
-      job.I = ctx->I; job.NW = nw; job.w0 = w0; job.W = W; job.C = ctx->C; job.L = ctx->L;
+      const JobView job = job_view(ctx, nw, w0, W, pulse_g, pulse_w);
       for (int32_t l = 1; l <= ctx->D; ++l) {
         PropParams p{};
         p.job = job;
@@ -531,8 +581,13 @@ int simulate_impl(gatspi_ctx* ctx, const gatspi_opts* opts) {
         p.seg.n_tiles = (int32_t)level_tiles(ctx->lvl_gate_begin[l + 1] - ctx->lvl_gate_begin[l], nw, ipt);
         p.tile_counter = ctx->d_tile_counter + l;
         if (o.time_kernels && (e = rec(ctx->ev[2 * l]))) return e;
-        SingleLaunch go{&p, ctx->stream};
-        launch_variant(nt, ipt, go);
+        if (pp) {
+          SingleLaunchMode<kModePulse> go{&p, ctx->stream};
+          launch_variant_pp(nt, ipt, go);
+        } else {
+          SingleLaunch go{&p, ctx->stream};
+          launch_variant(nt, ipt, go);
+        }
         if ((e = cudaGetLastError())) return e;
         if (o.time_kernels && (e = rec(ctx->ev[2 * l + 1]))) return e;
       }
@@ -561,9 +616,9 @@ int simulate_impl(gatspi_ctx* ctx, const gatspi_opts* opts) {
     const std::vector<long long> key = {
         ctx->generation, (long long)(uintptr_t)ctx->d_arena, (long long)ctx->arena_bytes, ctx->times_cap,
         nw, w0, W, nt, ipt, o.digest, o.time_kernels, record_first ? 1 : 0, l0, ctx->batch_T,
-        (long long)(uintptr_t)ctx->d_gate_delta};
+        (long long)(uintptr_t)ctx->d_gate_delta, pulse_g, pulse_w};
     bool done = false;
-    if (ctx->eager_nt == nt && ctx->eager_ipt == ipt) {  // the variant's attributes are set
+    if (ctx->eager_nt == nt && ctx->eager_ipt == ipt && ctx->eager_pp == pp) {  // the variant's attributes are set
       if (!(ctx->gexec && ctx->gkey == key)) {
         if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
         ctx->gexec = nullptr;
@@ -591,6 +646,7 @@ int simulate_impl(gatspi_ctx* ctx, const gatspi_opts* opts) {
       CK(enqueue(false));
       ctx->eager_nt = nt;
       ctx->eager_ipt = ipt;
+      ctx->eager_pp = pp;
     }
     if (record_first) first_recorded = true;
     st.kernel_launches += 1 + ctx->D + (o.digest ? 1 : 0);
@@ -670,6 +726,11 @@ int simulate_impl(gatspi_ctx* ctx, const gatspi_opts* opts) {
   ctx->stats = st;
   ctx->have_result = true;
   ctx->have_digest = o.digest != 0;
+  // the last batch stays resident: with one batch it is the whole result,
+  // which an edit can then update in place (gatspi_resimulate_edit)
+  ctx->result_single = st.batches == 1 && ctx->batch_T > 0 && ctx->window_limit == 0;
+  ctx->append_ptr = edges_total;
+  ctx->result_gen = ctx->generation;
   return GATSPI_OK;
 }
 
@@ -721,7 +782,8 @@ int gatspi_simulate(gatspi_ctx* ctx, const gatspi_opts* opts) {
     return fail(ctx, GATSPI_ESTATE, "load a netlist, its delays and a stimulus first");
   gatspi_opts o{};
   if (opts) o = *opts;
-  if (o.tile_items == 0 && o.items_per_thread == 0) {
+  const bool pp = o.pulse_limits == 1 && (o.gate_pulse_percent != 100 || o.wire_pulse_percent != 100);
+  if (o.tile_items == 0 && o.items_per_thread == 0 && !pp) {
     if (!ctx->tuned_nt) {
       const int rc = autotune(ctx, o);
       if (rc) return rc;
@@ -729,7 +791,197 @@ int gatspi_simulate(gatspi_ctx* ctx, const gatspi_opts* opts) {
     o.tile_items = ctx->tuned_nt;
     o.items_per_thread = ctx->tuned_ipt;
   }
-  return simulate_impl(ctx, &o);
+  const int rc = simulate_impl(ctx, &o);
+  if (rc == GATSPI_OK) {
+    ctx->last_opts = o;
+    ctx->last_opts.tile_items = ctx->stats.tile_threads;
+    ctx->last_opts.items_per_thread = ctx->stats.items_per_thread;
+  }
+  return rc;
+}
+
+int gatspi_resimulate_edit(gatspi_ctx* ctx, int32_t n_edits, const int32_t* edit_gate,
+                           const int32_t* edit_delta, gatspi_resim_info* info) {
+  if (!ctx) return GATSPI_EINVAL;
+  if (!ctx->have_result) return fail(ctx, GATSPI_ESTATE, "simulate once before re-simulating an edit");
+  std::vector<int32_t> nd;
+  int rc = edit_vector(ctx, n_edits, edit_gate, edit_delta, &nd);
+  if (rc) return rc;
+  gatspi_resim_info r{};
+  const auto t_start = std::chrono::steady_clock::now();
+  const bool resident = ctx->result_single && ctx->result_gen == ctx->generation;
+  // gates whose delays change: the cone's roots
+  std::vector<uint8_t> in_cone(ctx->G, 0);
+  int32_t roots = 0;
+  for (int32_t g = 0; g < ctx->G; ++g) {
+    const int32_t a = ctx->delta.empty() ? 0 : ctx->delta[g];
+    const int32_t b = nd.empty() ? 0 : nd[g];
+    if (a != b) {
+      in_cone[g] = 1;
+      ++roots;
+    }
+  }
+  ctx->generation++;
+  if ((rc = apply_edit(ctx, std::move(nd)))) {
+    ctx->have_result = false;
+    return rc;
+  }
+  const gatspi_opts o = ctx->last_opts;
+  auto full = [&]() {
+    r.mode = 2;
+    const int e = simulate_impl(ctx, &o);
+    r.cone_gates = ctx->G;
+    r.first_level = 1;
+    r.levels = ctx->D;
+    r.items = (int64_t)ctx->G * ctx->n_windows;
+    if (info) *info = r;
+    return e;
+  };
+  if (roots == 0) {  // nothing changes: the resident result stands
+    if (resident) ctx->result_gen = ctx->generation;
+    if (info) *info = r;
+    return GATSPI_OK;
+  }
+  if (!resident) return full();
+  // the fanout cone of the changed gates, level by level (gates are sorted
+  // by level, so one pass in gate order reaches every cone gate after its
+  // fanins)
+  if (ctx->fo_ptr.empty()) {
+    ctx->fo_ptr.assign((size_t)ctx->N + 1, 0);
+    for (int32_t p = 0; p < ctx->P; ++p) ctx->fo_ptr[ctx->fanin_net[p] + 1]++;
+    for (int32_t n = 0; n < ctx->N; ++n) ctx->fo_ptr[n + 1] += ctx->fo_ptr[n];
+    ctx->fo_gate.assign((size_t)ctx->P, 0);
+    std::vector<int32_t> fill(ctx->fo_ptr.begin(), ctx->fo_ptr.end() - 1);
+    for (int32_t g = 0; g < ctx->G; ++g)
+      for (int32_t p = ctx->fanin_ptr[g]; p < ctx->fanin_ptr[g + 1]; ++p) ctx->fo_gate[fill[ctx->fanin_net[p]]++] = g;
+  }
+  std::vector<int32_t> list;
+  std::vector<int32_t> lvl_off((size_t)ctx->D + 2, 0);  // cone gates of level l: list[lvl_off[l] .. lvl_off[l+1])
+  for (int32_t l = 1; l <= ctx->D; ++l) {
+    lvl_off[l] = (int32_t)list.size();
+    for (int32_t g = ctx->lvl_gate_begin[l]; g < ctx->lvl_gate_begin[l + 1]; ++g) {
+      if (!in_cone[g]) continue;
+      list.push_back(g);
+      const int32_t net = ctx->I + g;
+      for (int32_t k = ctx->fo_ptr[net]; k < ctx->fo_ptr[net + 1]; ++k) in_cone[ctx->fo_gate[k]] = 1;
+    }
+  }
+  lvl_off[ctx->D + 1] = (int32_t)list.size();
+  const int32_t nw = ctx->batch_nw, T = ctx->batch_T;
+  // room for the cone's new runs: at least twice the edges the cone's nets
+  // hold now, else the whole batch is simulated again (which also compacts)
+  std::vector<unsigned long long> tc(ctx->N);
+  CK(cudaMemcpy(tc.data(), ctx->d_tc, sizeof(unsigned long long) * ctx->N, cudaMemcpyDeviceToHost));
+  int64_t old_edges = 0;
+  for (int32_t g : list) old_edges += (int64_t)tc[(size_t)ctx->I + g];
+  if (ctx->append_ptr + 2 * old_edges + (1 << 16) > ctx->times_cap) return full();
+  if (!ctx->d_cone) {
+    CK(cudaMalloc(&ctx->d_cone, sizeof(int32_t) * std::max<int32_t>(ctx->G, 1)));
+  }
+  if (!ctx->d_append) CK(cudaMalloc(&ctx->d_append, 2 * sizeof(long long)));
+  CK(cudaMemcpy(ctx->d_cone, list.data(), sizeof(int32_t) * list.size(), cudaMemcpyHostToDevice));
+  const long long ap = ctx->append_ptr;
+  CK(cudaMemcpy(ctx->d_append, &ap, sizeof(long long), cudaMemcpyHostToDevice));
+  const int32_t pulse_g = o.pulse_limits ? o.gate_pulse_percent : 100;
+  const int32_t pulse_w = o.pulse_limits ? o.wire_pulse_percent : 100;
+  const bool pp = pulse_g != 100 || pulse_w != 100;
+  const int nt = o.tile_items, ipt = o.items_per_thread;
+  if (ctx->ev.size() < 2) {
+    for (auto e : ctx->ev) cudaEventDestroy(e);
+    ctx->ev.assign(2, nullptr);
+    for (auto& e : ctx->ev) CK(cudaEventCreate(&e));
+  }
+  cudaEvent_t e0 = ctx->ev[0], e1 = ctx->ev[1];
+  CK(cudaMemsetAsync(ctx->d_status, 0, sizeof(int32_t), ctx->stream));
+  CK(cudaEventRecord(e0, ctx->stream));
+  clear_saif_kernel<<<(unsigned)((list.size() + 255) / 256), 256, 0, ctx->stream>>>(
+      (int32_t)list.size(), ctx->d_cone, ctx->I, ctx->d_t1, ctx->d_tc);
+  CK(cudaGetLastError());
+  const JobView job = job_view(ctx, nw, ctx->batch_w0, ctx->W, pulse_g, pulse_w);
+  int32_t k = 0;
+  for (int32_t l = 1; l <= ctx->D; ++l) {
+    const int32_t nc = lvl_off[l + 1] - lvl_off[l];
+    if (nc == 0) continue;
+    if (r.levels == 0) r.first_level = l;
+    CK(cudaMemsetAsync(ctx->d_counters + l, 0, sizeof(unsigned long long), ctx->stream));
+    CK(cudaMemsetAsync(ctx->d_tile_counter + l, 0, sizeof(int32_t), ctx->stream));
+    PropParams p{};
+    p.job = job;
+    p.seg.counters = ctx->d_counters + l;
+    p.seg.level = l;
+    p.seg.gate_begin = ctx->lvl_gate_begin[l];
+    p.seg.n_items = nc * nw;
+    p.seg.n_tiles = nc * T;
+    p.seg.gate_list = ctx->d_cone + lvl_off[l];
+    p.seg.append_in = ctx->d_append + (k & 1);
+    p.seg.append_out = ctx->d_append + ((k + 1) & 1);
+    p.tile_counter = ctx->d_tile_counter + l;
+    if (pp) {
+      SingleLaunchMode<kModePulse> go{&p, ctx->stream};
+      launch_variant_pp(nt, ipt, go);
+    } else {
+      SingleLaunchMode<kModeCone> go{&p, ctx->stream};
+      launch_variant_cone(ipt, go);
+    }
+    CK(cudaGetLastError());
+    ++k;
+    ++r.levels;
+    r.items += (int64_t)nc * nw;
+  }
+  CK(cudaEventRecord(e1, ctx->stream));
+  if (o.digest) {
+    CK(cudaMemsetAsync(ctx->d_digest, 0, sizeof(unsigned long long) * ctx->N, ctx->stream));
+    DigestParams q{};
+    q.rmeta = ctx->d_rmeta; q.tinfo = ctx->d_tinfo; q.rstart = ctx->d_rstart;
+    q.net_level = ctx->d_net_level; q.lvl_base = ctx->d_lvl_base; q.times = ctx->d_times;
+    q.capacity = ctx->times_cap; q.out = ctx->d_digest; q.status = ctx->d_status;
+    q.N = ctx->N; q.NW = nw; q.w0 = ctx->batch_w0;
+    q.TW = ctx->batch_TW;
+    q.T = T;
+    const long long warps = (long long)q.N * q.T;
+    digest_kernel<<<(unsigned)((warps + 7) / 8), 256, 0, ctx->stream>>>(q);
+    CK(cudaGetLastError());
+  }
+  CK(cudaMemcpyAsync(&ctx->h_ret[0], ctx->d_status, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaMemcpyAsync(&ctx->h_ret[1], ctx->d_append + (k & 1), sizeof(long long), cudaMemcpyDeviceToHost,
+                     ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  const int32_t status = (int32_t)ctx->h_ret[0];
+  if (status & kStTimeout) {
+    ctx->have_result = false;
+    return fail(ctx, GATSPI_ETIMEOUT, "a device-side wait ran out");
+  }
+  // a cone that outgrew the append region (or int32 run offsets): the whole
+  // batch again, from scratch
+  if (status & (kStCapacity | kStOffset | kStCorrupt)) return full();
+  ctx->append_ptr = ctx->h_ret[1];
+  ctx->result_gen = ctx->generation;
+  r.mode = 1;
+  r.cone_gates = (int32_t)list.size();
+  // figures of this call: the cone's launches
+  gatspi_stats st = ctx->stats;
+  float ms = 0;
+  CK(cudaEventElapsedTime(&ms, e0, e1));
+  st.prop_ms = ms;
+  st.device_ms = ms;
+  st.input_ms = 0;
+  st.kernel_launches = 1 + r.levels + (o.digest ? 1 : 0);
+  st.prop_launches = r.levels;
+  st.items = r.items;
+  CK(cudaMemcpy(tc.data(), ctx->d_tc, sizeof(unsigned long long) * ctx->N, cudaMemcpyDeviceToHost));
+  int64_t edges = 0, bytes = 0;
+  for (int32_t n = 0; n < ctx->N; ++n) edges += (int64_t)tc[n];
+  for (int32_t g : list) {
+    const int32_t pins = ctx->fanin_ptr[g + 1] - ctx->fanin_ptr[g];
+    bytes += (int64_t)(pins + 1) * (2ll * nw + 8ll * T) + 4ll * (int64_t)tc[(size_t)ctx->I + g];
+    for (int32_t p = ctx->fanin_ptr[g]; p < ctx->fanin_ptr[g + 1]; ++p) bytes += 4ll * (int64_t)tc[ctx->fanin_net[p]];
+  }
+  st.edges = edges;
+  st.algo_bytes = bytes;
+  st.wall_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
+  ctx->stats = st;
+  if (info) *info = r;
+  return GATSPI_OK;
 }
 
 int gatspi_saif(gatspi_ctx* ctx, int64_t* t0, int64_t* t1, int64_t* tc) {

@@ -81,6 +81,10 @@ struct JobView {
   // window w of the batch is global window w0 + w; it spans cycles
   // [g*W, min(g*W + W, C)) of L ps each
   int32_t w0, W, C, L;
+  // pulse limits of the gate and interconnect inertial tests, percent of
+  // the delay (read only by the kernels compiled with pulse limits; the
+  // others apply Algorithm 1 as printed, i.e. 100 / 100)
+  int32_t pulse_g, pulse_w;
 };
 
 // One level of one job inside a launch.
@@ -90,6 +94,17 @@ struct SegView {
   int32_t gate_begin;  // first internal gate of the level
   int32_t n_items;     // gates of the level * NW
   int32_t n_tiles;
+  // Re-simulation of a fanout cone (gate-aligned tiling only), null
+  // otherwise: the tiles cover the listed gates (internal ids) instead of
+  // all the level's gates, and their edges go to an append region past
+  // everything stored, so that the other gates' waveforms stay in place.
+  // The launch's edges start at *append_in; its last tile writes where the
+  // next launch's start to *append_out (consecutive launches swap the two
+  // words) and leaves lvl_base alone.  Tile runs stay relative to
+  // lvl_base[level].
+  const int32_t* gate_list;
+  const long long* append_in;
+  long long* append_out;
 };
 
 struct PropParams {
@@ -220,6 +235,103 @@ __device__ __forceinline__ void run_gate(Pin (&pin)[K], uint32_t lut,
   t1 = acc;
 }
 
+// Interconnect test with a pulse limit of pw percent (Section 3 allows
+// PATHPULSEPERCENT values other than 100): the pulse (j, j+1) is dropped
+// when 100 (t_{j+1} - t_j) < pw delta(e_j), or when its two delayed edges
+// would not stay in order (a width of zero or less after the delays, which
+// the 100 percent test already covers); repeated until an edge survives.
+__device__ __forceinline__ void pin_advance_pp(Pin& q, int32_t pw) {
+  int32_t j = q.j, a = kInf;
+  while (j < q.n) {
+    const int32_t t = q.t[j];
+    const bool rise = ((q.v0 ^ (uint32_t)j) & 1u) == 0u;
+    const int32_t d = rise ? q.dr : q.df;
+    if (j + 1 < q.n) {
+      const int32_t t2 = q.t[j + 1];
+      const int32_t d2 = rise ? q.df : q.dr;
+      if (100ll * (t2 - t) < (long long)pw * d || t2 + d2 <= t + d) {
+        j += 2;
+        continue;
+      }
+    }
+    a = t + d;
+    ++j;
+    break;
+  }
+  q.j = j;
+  q.a = a;
+}
+
+// Algorithm 1 with pulse limits: pg percent for the gate test (cancel the
+// last kept output edge E when 100 (t_o - E) < pg gateDelay, or t_o <= E)
+// and pw percent for the interconnect test.  Below 100 percent a cancel
+// can expose a kept edge that is itself still cancellable, so the kept
+// edges form a stack (the paper's p_o moving back): the top lives in a
+// register, the ones below it in the sink, which reads them back.  T1 is
+// kept as y0 * len plus one signed term per kept edge (a rising edge at t
+// adds len - min(t, len), a falling one subtracts it), so a cancel takes
+// its edge's term back out.
+template <int K, class Sink>
+__device__ __forceinline__ void run_gate_pp(Pin (&pin)[K], uint32_t lut, const int32_t* __restrict__ gd,
+                                            int32_t edit, int32_t len, int32_t pg, int32_t pw, Sink& sink,
+                                            int32_t& count, int32_t& t1, uint32_t& y0) {
+  uint32_t col = 0;
+#pragma unroll
+  for (int i = 0; i < K; ++i) col |= (pin[i].v0 & 1u) << i;
+  uint32_t y = (lut >> col) & 1u;
+  y0 = y;
+#pragma unroll
+  for (int i = 0; i < K; ++i) pin_advance_pp(pin[i], pw);
+  int32_t n = 0;  // kept edges below the top (in the sink)
+  bool top_on = false;
+  int32_t top = 0;
+  long long acc = y ? (long long)len : 0ll;
+  auto term = [&](int32_t k, int32_t te) -> long long {  // signed T1 term of kept edge k
+    const long long r = (long long)len - min(te, len);
+    return ((y0 ^ (uint32_t)k) & 1u) ? -r : r;
+  };
+  for (;;) {
+    int32_t t = pin[0].a;
+#pragma unroll
+    for (int i = 1; i < K; ++i) t = min(t, pin[i].a);
+    if (t == kInf) break;
+    int istar = 0;
+#pragma unroll
+    for (int i = 0; i < K; ++i) {
+      if (pin[i].a == t) {  // every pin arriving now switches (MSI)
+        col ^= 1u << i;
+        istar = i;
+        pin_advance_pp(pin[i], pw);
+      }
+    }
+    const uint32_t yn = (lut >> col) & 1u;
+    if (yn != y) {
+      const uint32_t side = (col & ((1u << istar) - 1u)) | ((col >> (istar + 1)) << istar);
+      const uint32_t ie = (col >> istar) & 1u;
+      const int32_t d = max(1, gd[istar * 32 + (int)(ie * 16u + yn * 8u + side)] + edit);
+      const int32_t to = t + d;
+      if (top_on && (100ll * (to - top) < (long long)pg * d || to <= top)) {
+        acc -= term(n, top);  // cancel the last kept edge
+        if (n > 0) {
+          --n;
+          top = sink.get(n);
+        } else {
+          top_on = false;
+        }
+      } else {
+        if (top_on) sink.put(n++, top);
+        top = to;
+        top_on = true;
+        acc += term(n, to);
+      }
+      y = yn;
+    }
+  }
+  if (top_on) sink.put(n++, top);
+  count = n;
+  t1 = (int32_t)acc;
+}
+
 // Appends a lane's output edges to its column of its warp's staging buffer
 // (element k of lane l's column at [k * 32 + l]); edges past the cap are
 // dropped and the lane simulates again straight to global memory once its
@@ -239,6 +351,7 @@ struct GlobalSink {
   __device__ __forceinline__ void put(int k, int32_t t) {
     if (k < limit) dst[k] = t;
   }
+  __device__ __forceinline__ int32_t get(int k) const { return k < limit ? dst[k] : 0; }
 };
 
 // Record of (net, window): start (relative to its level's base), count and
@@ -620,6 +733,205 @@ __device__ __forceinline__ void load_desc(const JobView& J, int32_t g, GateDesc&
   }
 }
 
+// Simulation with pulse limits.  Below 100 percent a cancel can expose a
+// kept output edge that is itself still cancellable, so the kept edges are
+// a stack that must be read back, however deep it grows; staging columns of
+// a fixed size cannot hold it.  So each window is simulated straight into
+// global memory, into a slot sized by an upper bound of its output: every
+// kept output edge follows an arrival of at least one pin, so a window has
+// at most as many output edges as its pins have edges.
+
+// The gate-aligned tile's steps after the quiet windows are settled and the
+// others listed (steps 3 and 4 of wide_tile_k): the bounds are scanned in
+// window order and the tile claims their sum; every listed window is
+// simulated into its slot; then the windows' edges are moved down, in
+// window order, into one run (a slot never starts before its run position,
+// so in-order moves never overwrite edges not yet moved), leaving the
+// unused rest of the claim empty.
+template <int K, int IPT, class PinsOf>
+__device__ __forceinline__ void wide_tail_pp(const JobView& J, const SegView& S, int32_t g, int32_t tg,
+                                             int32_t wb, int32_t n, int32_t n_act, int lane, uint32_t lut,
+                                             const int32_t* gd, int32_t edit, long long acc_t1,
+                                             WarpSmem<IPT>& sm, PinsOf&& pins_of) {
+  // slot of each listed window: exclusive scan of the bounds (in sm.cnt)
+  int32_t U = 0;
+  for (int32_t r0 = 0; r0 < n_act; r0 += 32) {
+    const int32_t q = r0 + lane;
+    int32_t ub = 0, wl = 0;
+    if (q < n_act) {
+      wl = sm.list[q];
+#pragma unroll
+      for (int i = 0; i < K; ++i) ub += sm.smeta[i][wl] & kMaxCount;
+    }
+    int32_t incl = ub;
+#pragma unroll
+    for (int dd = 1; dd < 32; dd <<= 1) {
+      const int32_t v = __shfl_up_sync(0xffffffffu, incl, dd);
+      if (lane >= dd) incl += v;
+    }
+    if (q < n_act) sm.cnt[wl] = U + incl - ub;
+    U += __shfl_sync(0xffffffffu, incl, 31);
+  }
+  // claim the bound (the level's range, or the append region)
+  const long long lbase = __ldg(J.lvl_base + S.level);
+  const long long obase = S.append_in ? __ldg(S.append_in) : lbase;
+  unsigned long long old = 0;
+  if (lane == 0) old = atomicAdd(S.counters, (1ull << kTileShift) + (unsigned long long)U);
+  old = __shfl_sync(0xffffffffu, old, 0);
+  const long long start = (long long)(old & kEdgeMask);
+  if (lane == 0 && (long long)(old >> kTileShift) == (long long)S.n_tiles - 1) {
+    const long long tot = start + U;
+    if (tot > 0x7fffffffll) atomicOr(J.status, kStOffset);
+    if (S.append_in) *S.append_out = obase + tot;
+    else J.lvl_base[S.level + 1] = lbase + tot;
+    if (obase + tot > J.capacity) atomicOr(J.status, kStCapacity);
+  }
+  int32_t* dst = J.times + obase + start;
+  const long long room = J.capacity - obase - start;  // elements left in the arena
+  __syncwarp();
+  for (int32_t q = lane; q < n_act; q += 32) {
+    const int32_t wl = sm.list[q];
+    const int32_t at = sm.cnt[wl];
+    Pin pin[K];
+    pins_of(wl, pin);
+    GlobalSink sink{dst + at, room - at};
+    int32_t c = 0, t1 = 0;
+    uint32_t y0 = 0;
+    run_gate_pp<K>(pin, lut, gd, edit, window_len(J.w0 + wb + wl, J.W, J.C, J.L), J.pulse_g, J.pulse_w, sink,
+                   c, t1, y0);
+    acc_t1 += t1;
+    sm.omet[wl] = (uint16_t)(min(c, kMaxCount) | (int32_t)(y0 << 15));
+    if (c > kMaxCount) atomicOr(J.status, kStOffset);
+  }
+  __syncwarp();  // every lane's edges and metas are visible to the warp
+  // move each window's edges from its slot to its place in the run
+  int32_t out_n = 0;
+  for (int32_t q = 0; q < n_act; ++q) {
+    const int32_t wl = sm.list[q];
+    const int32_t c = sm.omet[wl] & kMaxCount;
+    const int32_t from = sm.cnt[wl];
+    for (int32_t j0 = 0; j0 < c; j0 += 32) {
+      const int32_t j = j0 + lane;
+      int32_t v = 0;
+      const bool ok = j < c && from + j < room && out_n + j < room;
+      if (ok) v = dst[from + j];
+      __syncwarp();
+      if (ok) dst[out_n + j] = v;
+      __syncwarp();
+    }
+    out_n += c;
+  }
+  {
+    uint16_t* om = J.rmeta + ((long long)J.I + g) * J.NW + wb;
+#pragma unroll
+    for (int k = 0; k < IPT; ++k)
+      if (k * 32 + lane < n) om[k * 32 + lane] = sm.omet[k * 32 + lane];
+  }
+  const long long rel = obase - lbase + start;
+  if (lane == 0) {
+    if (rel + out_n > 0x7fffffffll) atomicOr(J.status, kStOffset);
+    J.tinfo[((long long)J.I + g) * J.T + tg] = make_int2((int32_t)rel, out_n);
+  }
+#pragma unroll
+  for (int dd = 16; dd > 0; dd >>= 1) acc_t1 += __shfl_xor_sync(0xffffffffu, acc_t1, dd);
+  if (lane == 0) {
+    const long long net = (long long)J.I + g;
+    if (acc_t1) atomicAdd(J.saif_t1 + net, (unsigned long long)acc_t1);
+    if (out_n) atomicAdd(J.saif_tc + net, (unsigned long long)out_n);
+  }
+}
+
+// One item (gate g, window w) with pulse limits, straight into dst.
+template <int K>
+__device__ __forceinline__ int32_t simulate_item_pp(const JobView& J, int32_t g, int32_t w, int32_t* dst,
+                                                    long long limit, int32_t& t1, uint32_t& y0) {
+  GateCtx<K> c;
+  load_gate<K>(J, g, c);
+  Pin pin[K];
+#pragma unroll
+  for (int i = 0; i < K; ++i) {
+    int32_t s, n;
+    uint32_t v0;
+    load_record(J, c.rec[i] + w, c.base[i], s, n, v0);
+    pin[i] = Pin{J.times + c.base[i] + s, n, 0, kInf, c.dr[i], c.df[i], v0};
+  }
+  GlobalSink sink{dst, limit};
+  int32_t n = 0;
+  run_gate_pp<K>(pin, c.lut, c.gd, c.edit, window_len(J.w0 + w, J.W, J.C, J.L), J.pulse_g, J.pulse_w, sink, n,
+                 t1, y0);
+  return n;
+}
+
+// Linear tiling with pulse limits: every item gets a slot sized by its
+// bound, in item order; records point at their slots (records carry their
+// own starts here, so the slots need no compaction).
+template <int IPT>
+__device__ __forceinline__ void linear_tile_pp(const JobView& J, const SegView& S, int32_t tile) {
+  const int lane = threadIdx.x & 31;
+  const int32_t r0 = tile * (32 * IPT) + lane * IPT;  // this lane's first item
+  const int32_t n_mine = max(0, min(IPT, S.n_items - r0));
+  int32_t ub[IPT];
+  int32_t mine = 0;
+#pragma unroll
+  for (int m = 0; m < IPT; ++m) {
+    ub[m] = 0;
+    if (m < n_mine) {
+      const int32_t r = r0 + m, gl = r / J.NW, w = r - gl * J.NW, g = S.gate_begin + gl;
+      const int32_t p0 = __ldg(J.fanin_ptr + g), p1 = __ldg(J.fanin_ptr + g + 1);
+      for (int32_t p = p0; p < p1; ++p)
+        ub[m] += __ldg(J.rmeta + (long long)__ldg(J.fanin_net + p) * J.NW + w) & kMaxCount;
+      mine += ub[m];
+    }
+  }
+  int32_t incl = mine;
+#pragma unroll
+  for (int dd = 1; dd < 32; dd <<= 1) {
+    const int32_t v = __shfl_up_sync(0xffffffffu, incl, dd);
+    if (lane >= dd) incl += v;
+  }
+  const long long aggregate = __shfl_sync(0xffffffffu, incl, 31);
+  const long long base = __ldg(J.lvl_base + S.level);
+  const long long start = claim_range(J, S, lane, aggregate, base);
+  int32_t* dst = J.times + base + start;
+  const long long room = J.capacity - base - start;
+  long long o = incl - mine;
+  int32_t cur_gl = -1;
+  long long acc_t1 = 0, acc_tc = 0;
+  const long long rec_first = ((long long)J.I + S.gate_begin) * J.NW + r0;
+  for (int m = 0; m < n_mine; ++m) {
+    const int32_t r = r0 + m, gl = r / J.NW, w = r - gl * J.NW, g = S.gate_begin + gl;
+    if (gl != cur_gl) {
+      if (cur_gl >= 0) {
+        const long long net = (long long)J.I + S.gate_begin + cur_gl;
+        if (acc_t1) atomicAdd(J.saif_t1 + net, (unsigned long long)acc_t1);
+        if (acc_tc) atomicAdd(J.saif_tc + net, (unsigned long long)acc_tc);
+      }
+      cur_gl = gl;
+      acc_t1 = acc_tc = 0;
+    }
+    int32_t c = 0, t1 = 0;
+    uint32_t y0 = 0;
+    const long long lim = room - o < (long long)ub[m] ? room - o : (long long)ub[m];
+    switch (__ldg(J.fanin_ptr + g + 1) - __ldg(J.fanin_ptr + g)) {
+      case 1: c = simulate_item_pp<1>(J, g, w, dst + o, lim, t1, y0); break;
+      case 2: c = simulate_item_pp<2>(J, g, w, dst + o, lim, t1, y0); break;
+      case 3: c = simulate_item_pp<3>(J, g, w, dst + o, lim, t1, y0); break;
+      default: c = simulate_item_pp<4>(J, g, w, dst + o, lim, t1, y0); break;
+    }
+    if (start + o + c > 0x7fffffffll || c > kMaxCount) atomicOr(J.status, kStOffset);
+    J.rstart[rec_first + m] = (int32_t)(start + o);
+    J.rmeta[rec_first + m] = (uint16_t)(min(c, kMaxCount) | (int32_t)(y0 << 15));
+    acc_t1 += t1;
+    acc_tc += c;
+    o += ub[m];
+  }
+  if (cur_gl >= 0) {
+    const long long net = (long long)J.I + S.gate_begin + cur_gl;
+    if (acc_t1) atomicAdd(J.saif_t1 + net, (unsigned long long)acc_t1);
+    if (acc_tc) atomicAdd(J.saif_tc + net, (unsigned long long)acc_tc);
+  }
+}
+
 // Gate-aligned tiling, up to K pins (pins from d.k on are absent: no edges,
 // value 0): tile tg of gate g, windows wb .. wb+n-1 (n <= TW).
 //  1. Everything that depends on the gate descriptor only is loaded at once:
@@ -637,15 +949,19 @@ __device__ __forceinline__ void load_desc(const JobView& J, int32_t g, GateDesc&
 //     while it is in flight, then the run (coalesced) and the tile's entry.
 //     If some lane's edges did not fit the staging, the listed windows are
 //     simulated again straight into their final place instead.
-template <int K, int IPT>
-__device__ __forceinline__ void wide_tile_k(const JobView& J, const SegView& S, const GateDesc& d, int32_t gl,
+// Kernel modes: Algorithm 1 as printed over all of a level's gates (the
+// benchmark kernel, which carries no code of the other modes), pulse limits
+// (with or without a gate list), and a gate list at 100 percent.
+constexpr int kModePlain = 0, kModePulse = 1, kModeCone = 2;
+
+template <int K, int IPT, int MODE>
+__device__ __forceinline__ void wide_tile_k(const JobView& J, const SegView& S, const GateDesc& d, int32_t g,
                                             int32_t tg, int32_t n, WarpSmem<IPT>& sm) {
   constexpr int CAP = WarpSmem<IPT>::CAP;
   constexpr int POOL = WarpSmem<IPT>::POOL;
   constexpr int OCAP = WarpSmem<IPT>::OCAP;
   constexpr int TW = WarpSmem<IPT>::TW;
   const int lane = threadIdx.x & 31;
-  const int32_t g = S.gate_begin + gl;
   const int32_t wb = tg * TW;
   const int32_t p0 = d.p0;
   const int kp = d.k;  // pins kp..K-1 are absent: no edges, value 0
@@ -761,6 +1077,11 @@ __device__ __forceinline__ void wide_tile_k(const JobView& J, const SegView& S, 
     }
   };
 
+  if constexpr (MODE == kModePulse) {
+    wide_tail_pp<K, IPT>(J, S, g, tg, wb, n, n_act, lane, lut, gd, edit, acc_t1, sm, pins_of);
+    return;
+  }
+
   // 3. listed windows, 32 per round, compacted in window order into cmp
   int32_t out_n = 0;    // the tile's edges so far
   bool spill = false;   // some round did not fit the staging (warp-uniform)
@@ -798,6 +1119,9 @@ __device__ __forceinline__ void wide_tile_k(const JobView& J, const SegView& S, 
 
   // 4. claim the run; store the metas while the claim is in flight
   const long long lbase = __ldg(J.lvl_base + S.level);
+  // where the launch's runs go: the level's range, or the append region
+  long long obase = lbase;
+  if constexpr (MODE != kModePlain) obase = S.append_in ? __ldg(S.append_in) : lbase;
   unsigned long long old = 0;
   if (lane == 0) old = atomicAdd(S.counters, (1ull << kTileShift) + (unsigned long long)out_n);
   {
@@ -808,18 +1132,20 @@ __device__ __forceinline__ void wide_tile_k(const JobView& J, const SegView& S, 
   }
   old = __shfl_sync(0xffffffffu, old, 0);
   const long long start = (long long)(old & kEdgeMask);
+  const long long rel = obase - lbase + start;  // the run's start relative to the level base
   if (lane == 0) {
     if ((long long)(old >> kTileShift) == (long long)S.n_tiles - 1) {
       const long long tot = start + out_n;
       if (tot > 0x7fffffffll) atomicOr(J.status, kStOffset);
-      J.lvl_base[S.level + 1] = lbase + tot;
-      if (lbase + tot > J.capacity) atomicOr(J.status, kStCapacity);
+      if (MODE != kModePlain && S.append_in) *S.append_out = obase + tot;
+      else J.lvl_base[S.level + 1] = lbase + tot;
+      if (obase + tot > J.capacity) atomicOr(J.status, kStCapacity);
     }
-    if (start + out_n > 0x7fffffffll) atomicOr(J.status, kStOffset);
-    J.tinfo[((long long)J.I + g) * J.T + tg] = make_int2((int32_t)start, out_n);
+    if (rel + out_n > 0x7fffffffll) atomicOr(J.status, kStOffset);
+    J.tinfo[((long long)J.I + g) * J.T + tg] = make_int2((int32_t)rel, out_n);
   }
-  int32_t* dst = J.times + lbase + start;
-  const long long room = J.capacity - lbase - start;  // elements left in the arena
+  int32_t* dst = J.times + obase + start;
+  const long long room = J.capacity - obase - start;  // elements left in the arena
   if (!spill) {
     const long long m = out_n < room ? out_n : (room > 0 ? room : 0);
     for (long long e = lane; e < m; e += 32) dst[e] = sm.cmp[e];
@@ -867,24 +1193,30 @@ __device__ __forceinline__ void wide_tile_k(const JobView& J, const SegView& S, 
   }
 }
 
-template <int IPT>
+template <int IPT, int MODE>
 __device__ __forceinline__ void wide_tile(const JobView& J, const SegView& S, int32_t tile, WarpSmem<IPT>& sm) {
   constexpr int TW = 32 * IPT;
   const int32_t gl = tile / J.T;
   const int32_t tg = tile - gl * J.T;
   const int32_t n = min(TW, J.NW - tg * TW);
+  int32_t g = S.gate_begin + gl;
+  if constexpr (MODE != kModePlain) {
+    if (S.gate_list) g = __ldg(S.gate_list + gl);
+  }
   GateDesc d;
-  load_desc(J, S.gate_begin + gl, d);
+  load_desc(J, g, d);
   // two compiled bodies, not four: 1- and 3-pin gates run with an absent
   // pin (measured 3% faster than four bodies: the hot code then fits the
   // instruction cache better)
-  if (d.k <= 2) wide_tile_k<2, IPT>(J, S, d, gl, tg, n, sm);
-  else wide_tile_k<4, IPT>(J, S, d, gl, tg, n, sm);
+  if (d.k <= 2) wide_tile_k<2, IPT, MODE>(J, S, d, g, tg, n, sm);
+  else wide_tile_k<4, IPT, MODE>(J, S, d, g, tg, n, sm);
 }
 
-template <int IPT>
+// Gate lists (fanout cones) exist for gate-aligned tiles only.
+template <int IPT, int MODE>
 __device__ __forceinline__ void propagate_warp(const JobView& J, const SegView& S, int32_t tile, WarpSmem<IPT>& sm) {
-  if (J.T > 0) wide_tile<IPT>(J, S, tile, sm);
+  if (J.T > 0) wide_tile<IPT, MODE>(J, S, tile, sm);
+  else if constexpr (MODE == kModePulse) linear_tile_pp<IPT>(J, S, tile);
   else linear_tile<IPT>(J, S, tile, sm);
 }
 
@@ -902,8 +1234,10 @@ __host__ __device__ constexpr int min_blocks() {
 }
 
 // One level of one job; each warp takes one tile (one atomic per block hands
-// out NT/32 consecutive tiles).
-template <int NT, int IPT>
+// out NT/32 consecutive tiles).  MODE: kModePlain, or one of the modes with
+// pulse limits or gate lists (separate instantiations, so the kernel for
+// Algorithm 1 as printed carries none of their code).
+template <int NT, int IPT, int MODE = kModePlain>
 __global__ void __launch_bounds__(NT, (min_blocks<NT, IPT>())) propagate_kernel(const __grid_constant__ PropParams p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   WarpSmem<IPT>* sm = reinterpret_cast<WarpSmem<IPT>*>(smem_raw);
@@ -912,7 +1246,7 @@ __global__ void __launch_bounds__(NT, (min_blocks<NT, IPT>())) propagate_kernel(
   __syncthreads();
   const int32_t t = s_first + (int32_t)(threadIdx.x >> 5);
   if (t >= p.seg.n_tiles) return;
-  propagate_warp<IPT>(p.job, p.seg, t, sm[threadIdx.x >> 5]);
+  propagate_warp<IPT, MODE>(p.job, p.seg, t, sm[threadIdx.x >> 5]);
 }
 
 // Several jobs (each at its own level) in one launch: tiles are handed out
@@ -933,7 +1267,7 @@ __global__ void __launch_bounds__(NT, (min_blocks<NT, IPT>())) propagate_multi_k
     if (m.segs[mid].tile_begin <= t) lo = mid; else hi = mid - 1;
   }
   const MultiSeg& sg = m.segs[lo];
-  propagate_warp<IPT>(sg.job, sg.seg, t - sg.tile_begin, sm[threadIdx.x >> 5]);
+  propagate_warp<IPT, kModePlain>(sg.job, sg.seg, t - sg.tile_begin, sm[threadIdx.x >> 5]);
 }
 
 // Items per tile (one warp's tile) for a variant.
@@ -969,6 +1303,51 @@ struct SingleLaunch {
     propagate_kernel<NT, IPT><<<grid, NT, dyn_smem<NT, IPT>(), s>>>(*p);
   }
 };
+
+// The kernels of the other modes, compiled for a few launch shapes only.
+template <int MODE>
+struct SingleLaunchMode {
+  const PropParams* p;
+  cudaStream_t s;
+  template <int NT, int IPT>
+  void go() {
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(propagate_kernel<NT, IPT, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)dyn_smem<NT, IPT>());
+      attr = true;
+    }
+    const unsigned grid = (unsigned)((p->seg.n_tiles + NT / 32 - 1) / (NT / 32));
+    propagate_kernel<NT, IPT, MODE><<<grid, NT, dyn_smem<NT, IPT>(), s>>>(*p);
+  }
+};
+
+// Pulse limits: 256 x {1, 2, 4} and 128 x 8.
+inline bool pulse_variant_compiled(int nt, int ipt) {
+  return (nt == 256 && (ipt == 1 || ipt == 2 || ipt == 4)) || (nt == 128 && ipt == 8);
+}
+
+inline bool launch_variant_pp(int nt, int ipt, SingleLaunchMode<kModePulse>& launch) {
+  switch (nt * 16 + ipt) {
+    case 256 * 16 + 1: launch.template go<256, 1>(); return true;
+    case 256 * 16 + 2: launch.template go<256, 2>(); return true;
+    case 256 * 16 + 4: launch.template go<256, 4>(); return true;
+    case 128 * 16 + 8: launch.template go<128, 8>(); return true;
+    default: return false;
+  }
+}
+
+// Gate lists at 100 percent: 256 threads, any windows per thread (a cone
+// must keep the tile width of the runs it updates).
+inline bool launch_variant_cone(int ipt, SingleLaunchMode<kModeCone>& launch) {
+  switch (ipt) {
+    case 1: launch.template go<256, 1>(); return true;
+    case 2: launch.template go<256, 2>(); return true;
+    case 4: launch.template go<256, 4>(); return true;
+    case 8: launch.template go<256, 8>(); return true;
+    default: return false;
+  }
+}
 
 struct MultiLaunch {
   const MultiParams* m;
@@ -1127,6 +1506,17 @@ __global__ void window_gather_kernel(int32_t N, int32_t NW, int32_t w, const int
   const int32_t* src = times + lvl_base[net_level[n]] + s;
   const long long d = dst_ptr[n];
   for (int32_t k = 0; k < c; ++k) out[d + k] = src[k];
+}
+
+// Clear the SAIF of the listed gates' nets before their cone is simulated
+// again (the new waveforms' SAIF is added by the propagation launches).
+__global__ void clear_saif_kernel(int32_t n, const int32_t* __restrict__ gates, int32_t I,
+                                  unsigned long long* t1, unsigned long long* tc) {
+  const int32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  const long long net = (long long)I + gates[k];
+  t1[net] = 0;
+  tc[net] = 0;
 }
 
 // Add a finished part's SAIF into its job's accumulators.

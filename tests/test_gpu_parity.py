@@ -55,8 +55,9 @@ def assert_saif_equal(sim, ref):
 @pytest.mark.parametrize("case", CASES, ids=[c["name"] for c in CASES])
 def test_hand_traced(case):
     wl = case_workload(case)
+    pulse = (case["pulse"]["gate"], case["pulse"]["wire"]) if "pulse" in case else None
     with gs.Simulator(wl.netlist, wl.delays, wl.stim) as sim:
-        sim.simulate(window_cycles=case["W"])
+        sim.simulate(window_cycles=case["W"], pulse=pulse)
         for e in case["expect"]:
             init, ptr, times = sim.window(e["window"])
             n = e["net"]
