@@ -191,6 +191,28 @@ int gatspi_set_stimulus(gatspi_ctx* ctx, int32_t num_cycles, int32_t cycle_ps,
                         const uint8_t* init, const int64_t* edge_ptr, const int32_t* edge_time);
 
 /*
+ * Set the input stimulus from a raw list of toggles, restructured on the
+ * device.  A waveform dump gives each input's changes as (input, time)
+ * pairs; cycle-parallel re-simulation needs them grouped per (input, cycle)
+ * in time order, relative to the cycle start -- the restructuring the paper
+ * does before its simulation kernels and counts in the application time
+ * (Sections 3 and 4).  Here the grouping runs on the GPU: a histogram of
+ * (input, cycle) buckets, an exclusive scan, a scatter, and a sort of each
+ * bucket's times.  The result is the same stimulus gatspi_set_stimulus
+ * takes (C cycles of L ps).
+ *   init        uint8 [I], value of each input at time 0
+ *   num_events  number of toggles (0 is allowed)
+ *   ev_input    int32 [num_events], the toggling input, in [0, I)
+ *   ev_time     int64 [num_events], ps from the start of cycle 0, in
+ *               [0, C*L); the events may come in any order
+ * Every event toggles its input.  The arrays are copied.  Errors: ESTATE
+ * (no netlist), EINVAL (an input id or a time out of range, an input that
+ * toggles twice at the same ps, bad init), ENOMEM, ECUDA.
+ */
+int gatspi_set_stimulus_events(gatspi_ctx* ctx, int32_t num_cycles, int32_t cycle_ps, const uint8_t* init,
+                               int64_t num_events, const int32_t* ev_input, const int64_t* ev_time);
+
+/*
  * Simulate every window (Algorithm 1 for every gate and window, level by
  * level; output storage claimed from the produced edge counts in the
  * same pass, where Section 3 counts, scans and stores in two) and accumulate SAIF.  Synchronous.  `opts` may be NULL.
@@ -271,6 +293,45 @@ int gatspi_read_window(gatspi_ctx* ctx, int32_t window, uint8_t* init, int64_t* 
 /* Figures of the last gatspi_simulate call.  Errors: EINVAL (NULL). */
 int gatspi_get_stats(gatspi_ctx* ctx, gatspi_stats* out);
 
+
+/* ------------------------------------------------------------------------
+ * File formats (host only: no context, no device).  The input waveforms of a
+ * re-simulation usually come from a VCD dump of an earlier simulation
+ * (Section 1: the waveforms of the sequential elements are known), and the
+ * results go to power analysis as a SAIF file (Section 3).
+ * ---------------------------------------------------------------------- */
+
+/*
+ * Read the input waveforms of `num_names` 1-bit signals from a VCD file.
+ * names[k] is a signal's reference name or its dot-separated path from the
+ * top scope ("top.u1.a"); it must match exactly one 1-bit $var.  The value
+ * of each signal at the end of time 0 is written to init[k]; every later
+ * time step whose final value differs from the one before is a toggle,
+ * written as (ev_input = k, ev_time = time in ps) in file (time) order --
+ * the arrays gatspi_set_stimulus_events takes.  Several changes of one
+ * signal at one time step count only by their final value.  Supported:
+ * $timescale of 1, 10 or 100 s, ms, us, ns or ps; $scope/$upscope; scalar
+ * changes and 1-bit vectors ("b1 id"); $dumpvars and the like.  Values x/z
+ * of a requested signal are rejected (2-value simulation, Section 2).
+ * `cap` is the size of ev_input / ev_time; *num_events receives the total.
+ * Errors: EINVAL (file, syntax, names, x/z, a first value after time 0),
+ * ECAPACITY (cap < total: call again with larger arrays).  A message goes
+ * to err (err_len bytes, may be NULL).
+ */
+int gatspi_vcd_read(const char* path, int32_t num_names, const char* const* names, uint8_t* init,
+                    int32_t* ev_input, int64_t* ev_time, int64_t cap, int64_t* num_events, char* err,
+                    int32_t err_len);
+
+/*
+ * Write SAIF (version 2.0, backward, TIMESCALE 1 ps) for `num_nets` nets of
+ * one instance `design`: per net T0, T1 and TC as gatspi_saif returns them
+ * (TX and IG are 0: 2-value simulation).  Names are written as SAIF
+ * identifiers, every character other than a letter, a digit or '_' escaped
+ * with a backslash.  Errors: EINVAL (arguments, file).
+ */
+int gatspi_saif_write(const char* path, const char* design, int64_t duration_ps, int32_t num_nets,
+                      const char* const* net_names, const int64_t* t0, const int64_t* t1, const int64_t* tc,
+                      char* err, int32_t err_len);
 
 /* ------------------------------------------------------------------------
  * Multi-job engine: batched and served re-simulation.

@@ -27,8 +27,9 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(_HERE)
 LIB_PATH = os.path.join(_HERE, "_build", "libgatspi.so")
 INCLUDE = os.path.join(ROOT, "include")
-SOURCES = [os.path.join(_HERE, "csrc", f) for f in ("gatspi.cu", "engine.cu", "noalloc.cu")]
-DEPS = SOURCES + [os.path.join(_HERE, "csrc", f) for f in ("kernels.cuh", "digest.cuh", "host_common.h")] + \
+SOURCES = [os.path.join(_HERE, "csrc", f) for f in ("gatspi.cu", "engine.cu", "noalloc.cu", "fileio.cpp")]
+DEPS = SOURCES + [os.path.join(_HERE, "csrc", f) for f in ("kernels.cuh", "digest.cuh", "ingest.cuh",
+                                                           "host_common.h")] + \
     [os.path.join(INCLUDE, "gatspi.h")]
 
 NVCC_FLAGS = ["-Xcompiler", "-fPIC", "-std=c++17",
@@ -45,7 +46,8 @@ EXPORTS = ["gatspi_create", "gatspi_destroy", "gatspi_last_error", "gatspi_load_
            "gatspi_engine_create", "gatspi_engine_destroy", "gatspi_engine_last_error",
            "gatspi_engine_add_netlist", "gatspi_engine_submit", "gatspi_engine_step",
            "gatspi_engine_drain", "gatspi_engine_poll", "gatspi_engine_release",
-           "gatspi_engine_get_stats", "gatspi_propagate_level_noalloc", "gatspi_resimulate_edit"]
+           "gatspi_engine_get_stats", "gatspi_propagate_level_noalloc", "gatspi_resimulate_edit",
+           "gatspi_set_stimulus_events", "gatspi_vcd_read", "gatspi_saif_write"]
 
 JOB_QUEUED, JOB_RUNNING, JOB_DONE, JOB_FAILED = 0, 1, 2, 3
 
@@ -160,6 +162,11 @@ def lib():
         L.gatspi_set_stimulus.argtypes = [vp, i32, i32, vp, vp, vp]
         L.gatspi_set_edit.argtypes = [vp, i32, vp, vp]
         L.gatspi_resimulate_edit.argtypes = [vp, i32, vp, vp, ctypes.POINTER(gatspi_resim_info)]
+        L.gatspi_set_stimulus_events.argtypes = [vp, i32, i32, vp, i64, vp, vp]
+        L.gatspi_vcd_read.argtypes = [ctypes.c_char_p, i32, vp, vp, vp, vp, i64,
+                                      ctypes.POINTER(ctypes.c_int64), ctypes.c_char_p, i32]
+        L.gatspi_saif_write.argtypes = [ctypes.c_char_p, ctypes.c_char_p, i64, i32, vp, vp, vp, vp,
+                                        ctypes.c_char_p, i32]
         L.gatspi_simulate.argtypes = [vp, ctypes.POINTER(gatspi_opts)]
         L.gatspi_saif.argtypes = [vp, vp, vp, vp]
         L.gatspi_read_window.argtypes = [vp, i32, vp, vp, vp, i64, ctypes.POINTER(ctypes.c_int64)]
@@ -245,6 +252,51 @@ def gatspi_resimulate_edit(ctx, edit_gate=None, edit_delta=None) -> dict:
     info = gatspi_resim_info()
     _check(ctx, lib().gatspi_resimulate_edit(ctx, n, _ptr(eg), _ptr(ed), ctypes.byref(info)))
     return info.as_dict()
+
+
+def gatspi_set_stimulus_events(ctx, num_cycles, cycle_ps, init, ev_input, ev_time) -> None:
+    """Stimulus from raw (input, absolute ps) toggles in any order,
+    restructured per (input, cycle) on the GPU."""
+    iv, ei, et = _arr(init, np.uint8), _arr(ev_input, np.int32), _arr(ev_time, np.int64)
+    _check(ctx, lib().gatspi_set_stimulus_events(ctx, int(num_cycles), int(cycle_ps), _ptr(iv),
+                                                 int(ei.shape[0]), _ptr(ei), _ptr(et)))
+
+
+def _names(names):
+    arr = (ctypes.c_char_p * len(names))(*[n.encode() for n in names])
+    return arr, ctypes.cast(arr, ctypes.c_void_p)
+
+
+def gatspi_vcd_read(path, names):
+    """(init uint8[k], ev_input int32[], ev_time int64[]) of the named 1-bit
+    signals of a VCD file (host only)."""
+    keep, pn = _names(list(names))
+    init = np.zeros(len(names), np.uint8)
+    total = ctypes.c_int64(0)
+    err = ctypes.create_string_buffer(512)
+    cap = 0
+    while True:
+        ei = np.empty(max(cap, 1), np.int32)
+        et = np.empty(max(cap, 1), np.int64)
+        rc = lib().gatspi_vcd_read(os.fsencode(path), len(names), pn, _ptr(init), _ptr(ei), _ptr(et), cap,
+                                   ctypes.byref(total), err, len(err))
+        if rc == ECAPACITY and total.value > cap:
+            cap = total.value
+            continue
+        if rc != OK:
+            raise GatspiError(rc, err.value.decode())
+        return init, ei[:total.value], et[:total.value]
+
+
+def gatspi_saif_write(path, design, duration_ps, names, t0, t1, tc) -> None:
+    """Write a SAIF file for the given nets (host only)."""
+    keep, pn = _names(list(names))
+    a, b, c = _arr(t0, np.int64), _arr(t1, np.int64), _arr(tc, np.int64)
+    err = ctypes.create_string_buffer(512)
+    rc = lib().gatspi_saif_write(os.fsencode(path), design.encode(), int(duration_ps), len(names), pn,
+                                 _ptr(a), _ptr(b), _ptr(c), err, len(err))
+    if rc != OK:
+        raise GatspiError(rc, err.value.decode())
 
 
 def gatspi_set_stimulus(ctx, num_cycles, cycle_ps, init, edge_ptr, edge_time) -> None:

@@ -14,6 +14,7 @@
 #include "host_common.h"
 #include "kernels.cuh"
 #include "digest.cuh"
+#include "ingest.cuh"
 
 using namespace gatspi_dev;
 
@@ -420,6 +421,83 @@ int gatspi_set_stimulus(gatspi_ctx* ctx, int32_t num_cycles, int32_t cycle_ps, c
   if ((rc = upload_reuse(ctx, ctx->d_edge_ptr, ctx->cap_edge_ptr, edge_ptr, (size_t)n + 1))) return rc;
   if ((rc = upload_reuse(ctx, ctx->d_edge_time, ctx->cap_edge_time, edge_time, (size_t)edge_ptr[n]))) return rc;
   if ((rc = upload_reuse(ctx, ctx->d_init_in, ctx->cap_init_in, init, (size_t)ctx->I))) return rc;
+  ctx->have_stim = true;
+  return GATSPI_OK;
+}
+
+int gatspi_set_stimulus_events(gatspi_ctx* ctx, int32_t num_cycles, int32_t cycle_ps, const uint8_t* init,
+                               int64_t num_events, const int32_t* ev_input, const int64_t* ev_time) {
+  if (!ctx) return GATSPI_EINVAL;
+  ctx->generation++;
+  if (!ctx->have_netlist) return fail(ctx, GATSPI_ESTATE, "load a netlist before the stimulus");
+  if (num_cycles < 1 || cycle_ps < 1) return fail(ctx, GATSPI_EINVAL, "num_cycles and cycle_ps must be >= 1");
+  if (!init || num_events < 0 || (num_events > 0 && (!ev_input || !ev_time)))
+    return fail(ctx, GATSPI_EINVAL, "null or negative stimulus arguments");
+  for (int32_t i = 0; i < ctx->I; ++i)
+    if (init[i] > 1) return fail(ctx, GATSPI_EINVAL, "initial values must be 0 or 1");
+  CK(cudaSetDevice(ctx->device));
+  ctx->have_stim = ctx->have_result = false;
+  const int64_t nb = (int64_t)ctx->I * num_cycles;  // (input, cycle) buckets
+  const int64_t n = num_events;
+  int32_t* d_in = nullptr;
+  int64_t* d_t = nullptr;
+  int32_t* d_cnt = nullptr;
+  long long* d_blk = nullptr;
+  const int64_t nblk = (nb + kScanItems - 1) / kScanItems;
+  auto cleanup = [&]() { dfree(d_in); dfree(d_t); dfree(d_cnt); dfree(d_blk); };
+  if (cudaMalloc(&d_in, sizeof(int32_t) * std::max<int64_t>(n, 1)) != cudaSuccess ||
+      cudaMalloc(&d_t, sizeof(int64_t) * std::max<int64_t>(n, 1)) != cudaSuccess ||
+      cudaMalloc(&d_cnt, sizeof(int32_t) * nb) != cudaSuccess ||
+      cudaMalloc(&d_blk, sizeof(long long) * std::max<int64_t>(nblk, 1)) != cudaSuccess) {
+    cudaGetLastError();
+    cleanup();
+    return fail(ctx, GATSPI_ENOMEM, "stimulus ingest buffers");
+  }
+  int rc = upload_reuse(ctx, ctx->d_edge_ptr, ctx->cap_edge_ptr, (const int64_t*)nullptr, (size_t)nb + 1);
+  if (!rc) rc = upload_reuse(ctx, ctx->d_edge_time, ctx->cap_edge_time, (const int32_t*)nullptr, (size_t)n);
+  if (!rc) rc = upload_reuse(ctx, ctx->d_init_in, ctx->cap_init_in, init, (size_t)ctx->I);
+  if (rc) {
+    cleanup();
+    return rc;
+  }
+  IngestParams q{};
+  q.ev_input = d_in; q.ev_time = d_t; q.n = n; q.I = ctx->I; q.C = num_cycles; q.L = cycle_ps;
+  q.counts = d_cnt; q.edge_ptr = ctx->d_edge_ptr; q.edge_time = ctx->d_edge_time; q.status = ctx->d_status;
+  std::vector<int64_t> ptr((size_t)nb + 1);
+  int32_t status = 0;
+  cudaStream_t st = ctx->stream;
+  const unsigned eb = (unsigned)std::max<int64_t>(1, (n + 255) / 256);
+  const unsigned bb = (unsigned)((nb + 255) / 256);
+  cudaError_t e = cudaSuccess;
+  do {
+    if (n && ((e = cudaMemcpyAsync(d_in, ev_input, sizeof(int32_t) * n, cudaMemcpyHostToDevice, st)) ||
+              (e = cudaMemcpyAsync(d_t, ev_time, sizeof(int64_t) * n, cudaMemcpyHostToDevice, st))))
+      break;
+    if ((e = cudaMemsetAsync(ctx->d_status, 0, sizeof(int32_t), st)) ||
+        (e = cudaMemsetAsync(d_cnt, 0, sizeof(int32_t) * nb, st)))
+      break;
+    if (n) ingest_bucket_kernel<<<eb, 256, 0, st>>>(q);
+    scan_totals_kernel<<<(unsigned)nblk, kScanThreads, 0, st>>>(d_cnt, nb, d_blk);
+    scan_blocks_kernel<<<1, kScanThreads, 0, st>>>(d_blk, nblk);
+    scan_apply_kernel<<<(unsigned)nblk, kScanThreads, 0, st>>>(d_cnt, nb, d_blk, ctx->d_edge_ptr);
+    if ((e = cudaMemsetAsync(d_cnt, 0, sizeof(int32_t) * nb, st))) break;
+    if (n) ingest_scatter_kernel<<<eb, 256, 0, st>>>(q);
+    ingest_order_kernel<<<bb, 256, 0, st>>>(q);
+    if ((e = cudaGetLastError())) break;
+    if ((e = cudaMemcpyAsync(&status, ctx->d_status, sizeof(int32_t), cudaMemcpyDeviceToHost, st)) ||
+        (e = cudaMemcpyAsync(ptr.data(), ctx->d_edge_ptr, sizeof(int64_t) * (nb + 1), cudaMemcpyDeviceToHost, st)) ||
+        (e = cudaStreamSynchronize(st)))
+      break;
+  } while (0);
+  cleanup();
+  if (e != cudaSuccess) return fail(ctx, GATSPI_ECUDA, std::string("stimulus ingest: ") + cudaGetErrorString(e));
+  if (status & kIngBadInput) return fail(ctx, GATSPI_EINVAL, "an event names an input outside [0, I)");
+  if (status & kIngBadTime) return fail(ctx, GATSPI_EINVAL, "an event time lies outside [0, num_cycles * cycle_ps)");
+  if (status & kIngTwice) return fail(ctx, GATSPI_EINVAL, "an input toggles twice at the same time");
+  ctx->C = num_cycles;
+  ctx->L = cycle_ps;
+  ctx->edge_ptr = std::move(ptr);
+  ctx->init_in.assign(init, init + ctx->I);
   ctx->have_stim = true;
   return GATSPI_OK;
 }
