@@ -350,6 +350,53 @@ def run_served_mode(args):
     print(json.dumps(line), flush=True)
 
 
+def run_ingest_mode(args):
+    """Stimulus ingest: the benchmark workload's 512 inputs x 10,000 cycles
+    as raw (input, absolute ps) toggles in shuffled order, restructured per
+    (input, cycle) on the GPU (gatspi_set_stimulus_events, host arrays in,
+    device stimulus out, copies included), against the per-cycle upload
+    (gatspi_set_stimulus, host validation) and the oracle's numpy
+    restructuring on the host."""
+    import gen
+    import paper_2203_06117_gb300 as gs
+    from oracle import stimulus as ostim
+    gs.build()
+    wl = gen.make_workload(WORKLOAD, seed=SEED, num_cycles=args.cycles or None)
+    st = wl.stim
+    inp, t = ostim.cycles_to_events(st)
+    perm = np.random.Generator(np.random.PCG64(SEED)).permutation(inp.size)
+    inp, t = np.ascontiguousarray(inp[perm]), np.ascontiguousarray(t[perm])
+    I = wl.netlist.num_inputs
+
+    def timed(fn, k):
+        out = []
+        for _ in range(k):
+            a = time.perf_counter()
+            fn()
+            out.append(time.perf_counter() - a)
+        return statistics.median(out)
+
+    with gs.Simulator(wl.netlist, wl.delays, st) as sim:
+        ev = lambda: gs.gatspi_set_stimulus_events(sim.ctx, st.num_cycles, st.cycle_ps, st.init, inp, t)
+        cyc = lambda: gs.gatspi_set_stimulus(sim.ctx, st.num_cycles, st.cycle_ps, st.init, st.edge_ptr,
+                                             st.edge_time)
+        for _ in range(args.warmup):
+            ev()
+            cyc()
+        t_ev = timed(ev, args.steps)
+        t_cyc = timed(cyc, args.steps)
+    t_host = timed(lambda: ostim.events_to_cycles(I, st.num_cycles, st.cycle_ps, inp, t), 3)
+    n = int(inp.size)
+    line = {"metric": "stimulus toggles restructured/s", "value": n / t_ev, "unit": "toggles/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_ev * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+            "config": {"workload": f"the mid workload's stimulus: {I} inputs x {st.num_cycles} cycles of "
+                                   f"{st.cycle_ps} ps, {n} toggles in shuffled order",
+                       "bytes_in": int(inp.nbytes + t.nbytes)},
+            "per_cycle_upload_ms": t_cyc * 1e3, "host_numpy_restructure_ms": t_host * 1e3}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -366,7 +413,7 @@ def main():
                     help="total oracle seconds of the reference arm (split over its steps)")
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--workload", default="mid", choices=["mid", "batched", "served"],
+    ap.add_argument("--workload", default="mid", choices=["mid", "batched", "served", "ingest"],
                     help="mid = the headline single-job benchmark; batched / served = the "
                          "multi-job engine against the plain per-job path")
     ap.add_argument("--scale", type=float, default=1.0, help="shrink batched/served workloads")
@@ -379,6 +426,8 @@ def main():
         return run_batched_mode(args)
     if args.workload == "served":
         return run_served_mode(args)
+    if args.workload == "ingest":
+        return run_ingest_mode(args)
     world, rank, local = dist_setup()
     if args.impl == "reference":
         run_reference(args, world, rank)

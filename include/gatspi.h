@@ -304,12 +304,13 @@ int gatspi_get_stats(gatspi_ctx* ctx, gatspi_stats* out);
 /*
  * Read the input waveforms of `num_names` 1-bit signals from a VCD file.
  * names[k] is a signal's reference name or its dot-separated path from the
- * top scope ("top.u1.a"); it must match exactly one 1-bit $var.  The value
- * of each signal at the end of time 0 is written to init[k]; every later
- * time step whose final value differs from the one before is a toggle,
- * written as (ev_input = k, ev_time = time in ps) in file (time) order --
- * the arrays gatspi_set_stimulus_events takes.  Several changes of one
- * signal at one time step count only by their final value.  Supported:
+ * top scope ("top.u1.a"); it must match exactly one 1-bit $var.  A
+ * signal's first value, at time 0, is its initial value (init[k]); every
+ * time step, time 0 included, whose final value differs from the value
+ * before it is a toggle, written as (ev_input = k, ev_time = time in ps) in
+ * file (time) order -- the arrays gatspi_set_stimulus_events takes.
+ * Several changes of one signal in one time step count only by their final
+ * value (a zero-width glitch is no toggle).  Supported:
  * $timescale of 1, 10 or 100 s, ms, us, ns or ps; $scope/$upscope; scalar
  * changes and 1-bit vectors ("b1 id"); $dumpvars and the like.  Values x/z
  * of a requested signal are rejected (2-value simulation, Section 2).

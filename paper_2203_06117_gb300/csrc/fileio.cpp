@@ -158,10 +158,10 @@ int gatspi_vcd_read(const char* path, int32_t num_names, const char* const* name
     }
   }
 
-  // value changes: the value of each input at the end of each time step;
-  // the values after time 0 are the initial values, and a later step whose
-  // final value differs from the one before is a toggle at that time
-  std::vector<int8_t> cur(num_names, -1), committed(num_names, -1);
+  // value changes: an input's first value, at time 0, is its initial value;
+  // every time step (time 0 included) whose final value differs from the
+  // value before the step is a toggle at that time
+  std::vector<int8_t> cur(num_names, -1), committed(num_names, -1), first(num_names, -1);
   std::vector<int32_t> touched;
   std::vector<uint8_t> is_touched(num_names, 0);
   int64_t now = 0, count = 0;
@@ -169,11 +169,6 @@ int gatspi_vcd_read(const char* path, int32_t num_names, const char* const* name
   auto commit = [&]() {
     for (int32_t k : touched) {
       is_touched[k] = 0;
-      if (now == 0 || committed[k] < 0) {
-        committed[k] = cur[k];
-        if (now != 0) return false;  // first value after time 0
-        continue;
-      }
       if (cur[k] != committed[k]) {
         if (count < cap) {
           ev_input[count] = k;
@@ -184,7 +179,6 @@ int gatspi_vcd_read(const char* path, int32_t num_names, const char* const* name
       }
     }
     touched.clear();
-    return true;
   };
   auto change = [&](char v, const std::string& code) -> int {
     auto it = code_inputs.find(code);
@@ -199,6 +193,14 @@ int gatspi_vcd_read(const char* path, int32_t num_names, const char* const* name
       return GATSPI_EINVAL;
     }
     for (int32_t k : it->second) {
+      if (committed[k] < 0) {  // the first value: the initial one, at time 0 only
+        if (now != 0) {
+          say(err, err_len, std::string("the first value of ") + names[k] + " comes after time 0");
+          return GATSPI_EINVAL;
+        }
+        first[k] = committed[k] = cur[k] = (int8_t)(v - '0');
+        continue;
+      }
       cur[k] = (int8_t)(v - '0');
       if (!is_touched[k]) {
         is_touched[k] = 1;
@@ -220,10 +222,7 @@ int gatspi_vcd_read(const char* path, int32_t num_names, const char* const* name
         say(err, err_len, "time goes back at '" + tok + "'");
         return GATSPI_EINVAL;
       }
-      if (have_time && t != now && !commit()) {
-        say(err, err_len, "an input's first value comes after time 0");
-        return GATSPI_EINVAL;
-      }
+      if (have_time && t != now) commit();
       if (!have_time && t != 0) {
         say(err, err_len, "the dump must start at #0");
         return GATSPI_EINVAL;
@@ -256,16 +255,13 @@ int gatspi_vcd_read(const char* path, int32_t num_names, const char* const* name
       tk.next(code);  // real values: never an input of interest
     }
   }
-  if (have_time && !commit()) {
-    say(err, err_len, "an input's first value comes after time 0");
-    return GATSPI_EINVAL;
-  }
+  if (have_time) commit();
   for (int32_t k = 0; k < num_names; ++k) {
-    if (committed[k] < 0) {
+    if (first[k] < 0) {
       say(err, err_len, std::string("no value at time 0 for ") + names[k]);
       return GATSPI_EINVAL;
     }
-    init[k] = (uint8_t)committed[k];
+    init[k] = (uint8_t)first[k];
   }
   *num_events = count;
   if (count > cap) {
