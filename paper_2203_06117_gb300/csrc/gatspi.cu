@@ -55,9 +55,9 @@ struct gatspi_ctx {
   int32_t* d_gate_delta = nullptr;  // delay edit per internal gate, or null
   int32_t max_edit = 0;
 
-  // stimulus
+  // stimulus (on the device only; the host reads back the few bounds a
+  // batch needs)
   int32_t C = 0, L = 0;
-  std::vector<int64_t> edge_ptr;
   int64_t* d_edge_ptr = nullptr;
   int32_t* d_edge_time = nullptr;
   uint8_t* d_init_in = nullptr;
@@ -74,6 +74,9 @@ struct gatspi_ctx {
   // into a CUDA graph): input prefixes, then status and the level end
   long long* h_in_prefix = nullptr;
   long long* h_ret = nullptr;  // [0] status, [1] edges of the batch
+  long long* h_bounds = nullptr;  // [2I] edges of each input before a batch's first and end cycle
+  long long* d_bounds = nullptr;
+  unsigned long long* d_first_bad = nullptr;  // stimulus check: first bad slot
   // the last batch captured into a graph, replayed while nothing it bakes
   // in changes (shape, stimulus, buffers)
   cudaGraphExec_t gexec = nullptr;
@@ -101,6 +104,7 @@ struct gatspi_ctx {
 
   // incremental re-simulation after a delay edit (gatspi_resimulate_edit)
   gatspi_opts last_opts{};         // options of the last gatspi_simulate, launch shape resolved
+  bool have_last_opts = false;
   int64_t result_gen = -1;         // generation the resident result belongs to
   bool result_single = false;      // the result is one resident batch with gate-aligned tiles
   int64_t append_ptr = 0;          // first element of times past every stored run
@@ -137,11 +141,14 @@ void dfree(T*& p) {
   p = nullptr;
 }
 
+// Host arrays go to the device on the context's stream, so that every
+// later kernel on that stream sees them; a copy from pageable memory is
+// staged before the call returns, so the caller may reuse its array.
 template <class T>
 int upload(gatspi_ctx* ctx, T*& dst, const T* src, size_t n) {
   dfree(dst);
   CK(cudaMalloc(&dst, std::max<size_t>(n, 1) * sizeof(T)));
-  if (src && n) CK(cudaMemcpy(dst, src, n * sizeof(T), cudaMemcpyHostToDevice));
+  if (src && n) CK(cudaMemcpyAsync(dst, src, n * sizeof(T), cudaMemcpyHostToDevice, ctx->stream));
   return GATSPI_OK;
 }
 
@@ -157,6 +164,7 @@ void free_netlist(gatspi_ctx* c) {
   dfree(c->d_gate_delay); dfree(c->d_wire_delay); dfree(c->d_t1); dfree(c->d_tc); dfree(c->d_digest);
   c->have_digest = false;
   dfree(c->d_in_prefix);
+  dfree(c->d_bounds);
 }
 
 void free_stim(gatspi_ctx* c) {
@@ -173,7 +181,7 @@ int upload_reuse(gatspi_ctx* ctx, T*& dst, size_t& cap, const T* src, size_t n) 
     CK(cudaMalloc(&dst, std::max<size_t>(n, 1) * sizeof(T)));
     cap = std::max<size_t>(n, 1);
   }
-  if (src && n) CK(cudaMemcpy(dst, src, n * sizeof(T), cudaMemcpyHostToDevice));
+  if (src && n) CK(cudaMemcpyAsync(dst, src, n * sizeof(T), cudaMemcpyHostToDevice, ctx->stream));
   return GATSPI_OK;
 }
 
@@ -313,7 +321,9 @@ int gatspi_destroy(gatspi_ctx* ctx) {
   dfree(ctx->d_append);
   if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
   if (ctx->h_in_prefix) cudaFreeHost(ctx->h_in_prefix);
+  if (ctx->h_bounds) cudaFreeHost(ctx->h_bounds);
   if (ctx->h_ret) cudaFreeHost(ctx->h_ret);
+  dfree(ctx->d_first_bad);
   for (auto e : ctx->ev) cudaEventDestroy(e);
   if (ctx->stream) cudaStreamDestroy(ctx->stream);
   delete ctx;
@@ -360,6 +370,10 @@ int gatspi_load_netlist(gatspi_ctx* ctx, int32_t num_inputs, int32_t num_gates,
   if (ctx->h_in_prefix) cudaFreeHost(ctx->h_in_prefix);
   ctx->h_in_prefix = nullptr;
   CK(cudaMallocHost(&ctx->h_in_prefix, sizeof(long long) * std::max<int32_t>(ctx->I, 1)));
+  if (ctx->h_bounds) cudaFreeHost(ctx->h_bounds);
+  ctx->h_bounds = nullptr;
+  CK(cudaMallocHost(&ctx->h_bounds, 2 * sizeof(long long) * std::max<int32_t>(ctx->I, 1)));
+  if ((rc = upload<long long>(ctx, ctx->d_bounds, nullptr, 2 * (size_t)ctx->I))) return rc;
   ctx->have_netlist = true;
   return GATSPI_OK;
 }
@@ -406,21 +420,45 @@ int gatspi_set_stimulus(gatspi_ctx* ctx, int32_t num_cycles, int32_t cycle_ps, c
   if (!ctx) return GATSPI_EINVAL;
   ctx->generation++;
   if (!ctx->have_netlist) return fail(ctx, GATSPI_ESTATE, "load a netlist before the stimulus");
-  const std::string why =
-      gatspi_host::validate_stimulus(ctx->I, num_cycles, cycle_ps, init, edge_ptr, edge_time);
-  if (!why.empty()) return fail(ctx, GATSPI_EINVAL, why);
-  CK(cudaSetDevice(ctx->device));
+  // the arrays' shape on the host; their contents are checked on the device
+  if (num_cycles < 1 || cycle_ps < 1) return fail(ctx, GATSPI_EINVAL, "num_cycles and cycle_ps must be >= 1");
+  if (!init || !edge_ptr) return fail(ctx, GATSPI_EINVAL, "null stimulus array");
   const int64_t n = (int64_t)ctx->I * num_cycles;
+  if (edge_ptr[0] != 0) return fail(ctx, GATSPI_EINVAL, "edge_ptr[0] must be 0");
+  const int64_t total = edge_ptr[n];
+  if (total < 0) return fail(ctx, GATSPI_EINVAL, "edge_ptr must be non-decreasing");
+  if (total > 0 && !edge_time) return fail(ctx, GATSPI_EINVAL, "null edge_time");
+  for (int32_t i = 0; i < ctx->I; ++i)
+    if (init[i] > 1) return fail(ctx, GATSPI_EINVAL, "initial values must be 0 or 1");
+  CK(cudaSetDevice(ctx->device));
   ctx->have_stim = ctx->have_result = false;
-  ctx->C = num_cycles;
-  ctx->L = cycle_ps;
-  ctx->edge_ptr.assign(edge_ptr, edge_ptr + n + 1);
-  ctx->init_in.assign(init, init + ctx->I);
   int rc;
   // device buffers are kept and reused while they are large enough
   if ((rc = upload_reuse(ctx, ctx->d_edge_ptr, ctx->cap_edge_ptr, edge_ptr, (size_t)n + 1))) return rc;
-  if ((rc = upload_reuse(ctx, ctx->d_edge_time, ctx->cap_edge_time, edge_time, (size_t)edge_ptr[n]))) return rc;
+  if ((rc = upload_reuse(ctx, ctx->d_edge_time, ctx->cap_edge_time, edge_time, (size_t)total))) return rc;
   if ((rc = upload_reuse(ctx, ctx->d_init_in, ctx->cap_init_in, init, (size_t)ctx->I))) return rc;
+  if (!ctx->d_first_bad) CK(cudaMalloc(&ctx->d_first_bad, sizeof(unsigned long long)));
+  const unsigned long long none = ~0ull;
+  CK(cudaMemsetAsync(ctx->d_status, 0, sizeof(int32_t), ctx->stream));
+  CK(cudaMemcpyAsync(ctx->d_first_bad, &none, sizeof(none), cudaMemcpyHostToDevice, ctx->stream));
+  stimulus_check_kernel<<<(unsigned)((n + 255) / 256), 256, 0, ctx->stream>>>(
+      ctx->d_edge_ptr, ctx->d_edge_time, n, total, cycle_ps, ctx->d_status, ctx->d_first_bad);
+  CK(cudaGetLastError());
+  int32_t status = 0;
+  unsigned long long bad = 0;
+  CK(cudaMemcpyAsync(&status, ctx->d_status, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaMemcpyAsync(&bad, ctx->d_first_bad, sizeof(bad), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (status) {
+    const std::string where = " (input " + std::to_string(bad / (unsigned long long)num_cycles) + " cycle " +
+                              std::to_string(bad % (unsigned long long)num_cycles) + ")";
+    if (status & kStimOrder) return fail(ctx, GATSPI_EINVAL, "edge_ptr must be non-decreasing" + where);
+    if (status & kStimRange) return fail(ctx, GATSPI_EINVAL, "edge time outside [0, cycle_ps)" + where);
+    return fail(ctx, GATSPI_EINVAL, "edge times must increase strictly within a cycle" + where);
+  }
+  ctx->C = num_cycles;
+  ctx->L = cycle_ps;
+  ctx->init_in.assign(init, init + ctx->I);
   ctx->have_stim = true;
   return GATSPI_OK;
 }
@@ -463,7 +501,6 @@ int gatspi_set_stimulus_events(gatspi_ctx* ctx, int32_t num_cycles, int32_t cycl
   IngestParams q{};
   q.ev_input = d_in; q.ev_time = d_t; q.n = n; q.I = ctx->I; q.C = num_cycles; q.L = cycle_ps;
   q.counts = d_cnt; q.edge_ptr = ctx->d_edge_ptr; q.edge_time = ctx->d_edge_time; q.status = ctx->d_status;
-  std::vector<int64_t> ptr((size_t)nb + 1);
   int32_t status = 0;
   cudaStream_t st = ctx->stream;
   const unsigned eb = (unsigned)std::max<int64_t>(1, (n + 255) / 256);
@@ -485,7 +522,6 @@ int gatspi_set_stimulus_events(gatspi_ctx* ctx, int32_t num_cycles, int32_t cycl
     ingest_order_kernel<<<bb, 256, 0, st>>>(q);
     if ((e = cudaGetLastError())) break;
     if ((e = cudaMemcpyAsync(&status, ctx->d_status, sizeof(int32_t), cudaMemcpyDeviceToHost, st)) ||
-        (e = cudaMemcpyAsync(ptr.data(), ctx->d_edge_ptr, sizeof(int64_t) * (nb + 1), cudaMemcpyDeviceToHost, st)) ||
         (e = cudaStreamSynchronize(st)))
       break;
   } while (0);
@@ -496,7 +532,6 @@ int gatspi_set_stimulus_events(gatspi_ctx* ctx, int32_t num_cycles, int32_t cycl
   if (status & kIngTwice) return fail(ctx, GATSPI_EINVAL, "an input toggles twice at the same time");
   ctx->C = num_cycles;
   ctx->L = cycle_ps;
-  ctx->edge_ptr = std::move(ptr);
   ctx->init_in.assign(init, init + ctx->I);
   ctx->have_stim = true;
   return GATSPI_OK;
@@ -604,13 +639,21 @@ int simulate_impl(gatspi_ctx* ctx, const gatspi_opts* opts) {
       NW = (NW + 1) / 2;
       continue;
     }
-    // level 0 from the stimulus
+    // level 0 from the stimulus: each input's edges in the batch, from the
+    // device copy of edge_ptr
     std::vector<long long> in_prefix(ctx->I);
     long long l0 = 0;
     const int32_t c_begin = w0 * W, c_end = std::min((w0 + nw) * W, ctx->C);
+    stimulus_bounds_kernel<<<(unsigned)((ctx->I + 255) / 256), 256, 0, ctx->stream>>>(
+        ctx->I, ctx->C, c_begin, c_end, ctx->d_edge_ptr, ctx->d_bounds);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(ctx->h_bounds, ctx->d_bounds, 2 * sizeof(long long) * ctx->I, cudaMemcpyDeviceToHost,
+                       ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    st.kernel_launches += 1;
     for (int32_t i = 0; i < ctx->I; ++i) {
       in_prefix[i] = l0;
-      l0 += ctx->edge_ptr[(size_t)i * ctx->C + c_end] - ctx->edge_ptr[(size_t)i * ctx->C + c_begin];
+      l0 += ctx->h_bounds[2 * i + 1] - ctx->h_bounds[2 * i];
     }
     if (l0 > ctx->times_cap || l0 > 0x7fffffffll) {
       if (NW > 1) { NW = (NW + 1) / 2; continue; }
@@ -871,6 +914,7 @@ int gatspi_simulate(gatspi_ctx* ctx, const gatspi_opts* opts) {
   }
   const int rc = simulate_impl(ctx, &o);
   if (rc == GATSPI_OK) {
+    ctx->have_last_opts = true;
     ctx->last_opts = o;
     ctx->last_opts.tile_items = ctx->stats.tile_threads;
     ctx->last_opts.items_per_thread = ctx->stats.items_per_thread;
@@ -881,13 +925,16 @@ int gatspi_simulate(gatspi_ctx* ctx, const gatspi_opts* opts) {
 int gatspi_resimulate_edit(gatspi_ctx* ctx, int32_t n_edits, const int32_t* edit_gate,
                            const int32_t* edit_delta, gatspi_resim_info* info) {
   if (!ctx) return GATSPI_EINVAL;
-  if (!ctx->have_result) return fail(ctx, GATSPI_ESTATE, "simulate once before re-simulating an edit");
+  if (!ctx->have_last_opts) return fail(ctx, GATSPI_ESTATE, "simulate once before re-simulating an edit");
+  if (!ctx->have_netlist || !ctx->have_delays || !ctx->have_stim)
+    return fail(ctx, GATSPI_ESTATE, "load a netlist, its delays and a stimulus first");
   std::vector<int32_t> nd;
   int rc = edit_vector(ctx, n_edits, edit_gate, edit_delta, &nd);
   if (rc) return rc;
   gatspi_resim_info r{};
   const auto t_start = std::chrono::steady_clock::now();
-  const bool resident = ctx->result_single && ctx->result_gen == ctx->generation;
+  const bool resident = ctx->have_result && ctx->result_single && ctx->result_gen == ctx->generation;
+  const bool current = ctx->have_result;  // the results match the loaded inputs and edit
   // gates whose delays change: the cone's roots
   std::vector<uint8_t> in_cone(ctx->G, 0);
   int32_t roots = 0;
@@ -915,7 +962,7 @@ int gatspi_resimulate_edit(gatspi_ctx* ctx, int32_t n_edits, const int32_t* edit
     if (info) *info = r;
     return e;
   };
-  if (roots == 0) {  // nothing changes: the resident result stands
+  if (roots == 0 && current) {  // nothing changes: the results stand
     if (resident) ctx->result_gen = ctx->generation;
     if (info) *info = r;
     return GATSPI_OK;

@@ -167,5 +167,53 @@ __global__ void ingest_order_kernel(IngestParams q) {
     }
 }
 
+// Checks of a per-cycle stimulus on the device (gatspi_set_stimulus): every
+// (input, cycle) slot's edge range lies inside the edge list and does not go
+// back, and its times lie in [0, L) and increase strictly.  The first bad
+// slot is kept (atomicMin) for the error message.
+constexpr int kStimOrder = 8;      // edge_ptr goes back or leaves [0, total]
+constexpr int kStimRange = 16;     // a time outside [0, L)
+constexpr int kStimIncrease = 32;  // times not strictly increasing in a slot
+
+__global__ void stimulus_check_kernel(const int64_t* __restrict__ ptr, const int32_t* __restrict__ t,
+                                      long long nslots, long long total, int32_t L, int32_t* status,
+                                      unsigned long long* first_bad) {
+  const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= nslots) return;
+  const int64_t a = ptr[k], b = ptr[k + 1];
+  int bad = 0;
+  if (b < a || a < 0 || b > total) {
+    bad = kStimOrder;
+  } else {
+    int32_t prev = -1;
+    for (int64_t e = a; e < b; ++e) {
+      const int32_t x = t[e];
+      if (x < 0 || x >= L) {
+        bad = kStimRange;
+        break;
+      }
+      if (x <= prev) {
+        bad = kStimIncrease;
+        break;
+      }
+      prev = x;
+    }
+  }
+  if (bad) {
+    atomicOr(status, bad);
+    atomicMin(first_bad, (unsigned long long)k);
+  }
+}
+
+// Edges of each input before cycle c0 and before cycle c1 (the bounds of a
+// batch of windows), for the host's batch planning.
+__global__ void stimulus_bounds_kernel(int32_t I, int32_t C, int32_t c0, int32_t c1,
+                                       const int64_t* __restrict__ ptr, long long* out) {
+  const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= I) return;
+  out[2 * i] = ptr[(long long)i * C + c0];
+  out[2 * i + 1] = ptr[(long long)i * C + c1];
+}
+
 }  // namespace
 }  // namespace gatspi_dev

@@ -144,6 +144,23 @@ def test_falls_back_to_a_full_run_without_free_arena():
         _check_against_full_and_oracle(sim, wl, gates, [40, 40], windows=range(0, 200, 13))
 
 
+def test_falls_back_to_a_full_run_after_a_new_stimulus():
+    wl = gen.make_workload("tiny", seed=47, num_cycles=150)
+    wl2 = gen.make_workload("tiny", seed=48, num_cycles=150)
+    rng = np.random.Generator(np.random.PCG64(47))
+    with gs.Simulator(wl.netlist, wl.delays, wl.stim) as sim:
+        sim.simulate(window_cycles=1, digest=1)
+        st = wl2.stim                                   # same netlist, another stimulus
+        gs.gatspi_set_stimulus(sim.ctx, st.num_cycles, st.cycle_ps, st.init, st.edge_ptr, st.edge_time)
+        gates = _ext_gates_at_levels(wl, [9], rng)
+        info = sim.resimulate_edit(gates, [21])
+        assert info["mode"] == 2
+        wl_new = gen.Workload(wl.name, wl.netlist, wl.delays, st, 0, {})
+        _check_against_full_and_oracle(sim, wl_new, gates, [21], windows=range(0, 150, 10))
+        info = sim.resimulate_edit(gates, [21])         # the same edit again: nothing to do
+        assert info["mode"] == 0
+
+
 def test_resimulate_needs_a_simulation_and_valid_edits():
     wl = gen.make_workload("tiny", seed=46, num_cycles=70)
     with gs.Simulator(wl.netlist, wl.delays, wl.stim) as sim:

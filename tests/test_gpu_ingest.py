@@ -118,3 +118,34 @@ def test_vcd_file_to_saif_file(tmp_path):
     assert int(head["DURATION"]) == st.num_cycles * st.cycle_ps
     for n, nm in enumerate(net_names):
         assert nets[nm] == (int(r0[n]), int(r1[n]), 0, int(rc[n]), 0), nm
+
+
+def test_per_cycle_stimulus_is_checked_on_the_device():
+    """gatspi_set_stimulus checks its arrays' contents with a kernel: each
+    kind of fault is rejected and named with its input and cycle, and a
+    valid stimulus loaded afterwards simulates correctly."""
+    wl = gen.make_workload("tiny", seed=55, num_cycles=20)
+    st = wl.stim
+    C, L = st.num_cycles, st.cycle_ps
+    counts = np.diff(st.edge_ptr)
+    k = int(np.nonzero(counts >= 2)[0][0])        # the first slot with two edges
+    a = int(st.edge_ptr[k])
+    where = f"input {k // C} cycle {k % C}"
+    with gs.Simulator(wl.netlist, wl.delays, st) as sim:
+        et = st.edge_time.copy()
+        et[a + 1] = et[a]                          # not strictly increasing
+        et2 = st.edge_time.copy()
+        et2[a] = -1                                # before the cycle
+        et3 = st.edge_time.copy()
+        et3[a + 1] = L                             # after the cycle
+        ep = st.edge_ptr.copy()
+        ep[k + 1] = ep[k] - 1 if ep[k] > 0 else ep[k + 2] + 1   # edge_ptr goes back
+        for p, t, msg in [(st.edge_ptr, et, where), (st.edge_ptr, et2, where), (st.edge_ptr, et3, where),
+                          (ep, st.edge_time, "")]:
+            with pytest.raises(gs.GatspiError) as e:
+                gs.gatspi_set_stimulus(sim.ctx, C, L, st.init, p, t)
+            assert e.value.code == gs.EINVAL and msg in str(e.value), str(e.value)
+        gs.gatspi_set_stimulus(sim.ctx, C, L, st.init, st.edge_ptr, st.edge_time)
+        sim.simulate(window_cycles=1)
+        ref = oracle.EventSim(wl.netlist, wl.delays, st, W=1)
+        assert all(np.array_equal(x, y) for x, y in zip(sim.saif(), ref.saif()))
