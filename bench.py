@@ -232,7 +232,7 @@ def run_reference(args, world, rank):
     if rank != 0:
         return
     per_step = []
-    pool = OraclePool()
+    pool = OraclePool(cores=args.ref_cores or None)
     # whole run bounded to about ref_seconds of oracle work
     budget = args.ref_seconds / (args.warmup + args.steps)
     try:
@@ -397,6 +397,98 @@ def run_ingest_mode(args):
     print(json.dumps(line), flush=True)
 
 
+def _levels(netlist):
+    """Logic level of every gate (caller numbering)."""
+    I = netlist.num_inputs
+    lvl = np.zeros(netlist.num_nets, np.int64)
+    for g in range(netlist.num_gates):
+        a, b = netlist.fanin_ptr[g], netlist.fanin_ptr[g + 1]
+        lvl[I + g] = 1 + lvl[netlist.fanin_net[a:b]].max()
+    return lvl[I:]
+
+
+def run_resim_mode(args):
+    """Delay edits on the benchmark workload (Section 4's loop: simulate,
+    re-time a cell, simulate again): gatspi_resimulate_edit, which runs
+    only the fanout cone of the re-timed gate, against a full simulation
+    with the same edit, for one gate at each of several depths."""
+    import gen
+    import paper_2203_06117_gb300 as gs
+    gs.build()
+    wl = gen.make_workload(WORKLOAD, seed=SEED, num_cycles=args.cycles or None)
+    lvl = _levels(wl.netlist)
+    D = int(lvl.max())
+    rng = np.random.Generator(np.random.PCG64(SEED))
+    opts = dict(window_cycles=1, tile_items=args.tile or 256, items_per_thread=args.ipt or 4)
+    G, C = wl.netlist.num_gates, wl.stim.num_cycles
+    rows = []
+    with gs.Simulator(wl.netlist, wl.delays, wl.stim) as sim:
+        sim.simulate(**opts)
+        for frac in (0.1, 0.5, 0.9, 1.0):
+            L = max(1, min(D, int(round(frac * D))))
+            g = int(rng.choice(np.nonzero(lvl == L)[0]))
+            cone, full, modes = [], [], []
+            for k in range(args.warmup + args.steps):
+                a = time.perf_counter()
+                info = sim.resimulate_edit([g], [25 + (k % 2)])   # a new edit every time
+                dt = time.perf_counter() - a
+                modes.append(info["mode"])
+                if k >= args.warmup and info["mode"] == 1:     # cone runs only (not a fallback)
+                    cone.append(dt)
+            gs.gatspi_set_edit(sim.ctx, [g], [30])
+            for k in range(args.warmup + args.steps):
+                a = time.perf_counter()
+                sim.simulate(**opts)
+                dt = time.perf_counter() - a
+                if k >= args.warmup:
+                    full.append(dt)
+            gs.gatspi_set_edit(sim.ctx, [], [])
+            sim.simulate(**opts)                                   # resident again, no edit
+            rows.append({"level": L, "cone_gates": info["cone_gates"], "cone_items": info["items"],
+                         "modes": modes, "cone_ms": statistics.median(cone) * 1e3 if cone else None,
+                         "full_ms": statistics.median(full) * 1e3})
+    best = max(r["full_ms"] / r["cone_ms"] for r in rows if r["cone_ms"])
+    line = {"metric": "re-simulation after a one-gate delay edit, speedup over a full run", "value": best,
+            "unit": "x", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": min(r["cone_ms"] for r in rows if r["cone_ms"]), "higher_is_better": True,
+            "scaling": "weak",
+            "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": f"mid: {G} gates, depth {D}, {C} cycles; one gate re-timed by +25/26 ps "
+                                   "at each of four depths; host wall time of each call"},
+            "edits": rows}
+    print(json.dumps(line), flush=True)
+
+
+def run_pulse_mode(args):
+    """Throughput of the pulse-limit kernels (PATHPULSEPERCENT other than
+    100) on the benchmark workload, next to Algorithm 1 as printed."""
+    import gen
+    import paper_2203_06117_gb300 as gs
+    gs.build()
+    wl = gen.make_workload(WORKLOAD, seed=SEED, num_cycles=args.cycles or None)
+    G, C = wl.netlist.num_gates, wl.stim.num_cycles
+    rows = []
+    with gs.Simulator(wl.netlist, wl.delays, wl.stim) as sim:
+        for pulse in (None, (50, 100), (0, 0)):
+            opts = dict(window_cycles=1, tile_items=256, items_per_thread=4, time_kernels=1, pulse=pulse)
+            for _ in range(args.warmup):
+                sim.simulate(**opts)
+            ms = []
+            for _ in range(args.steps):
+                sim.simulate(**opts)
+                ms.append(sim.stats()["prop_ms"])
+            st = sim.stats()
+            rows.append({"limits": "100/100" if pulse is None else f"{pulse[0]}/{pulse[1]}",
+                         "prop_ms": statistics.median(ms), "edges": int(st["edges"]),
+                         "gate_cycles_per_s": G * C / (statistics.median(ms) / 1e3)})
+    line = {"metric": "gate*cycle evals/s with transport delay (pulse limits 0/0)",
+            "value": rows[-1]["gate_cycles_per_s"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": rows[-1]["prop_ms"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": f"mid: {G} gates x {C} cycles, 256 x 4 launch shape"}, "limits": rows}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -411,9 +503,11 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--ref-seconds", type=float, default=120.0,
                     help="total oracle seconds of the reference arm (split over its steps)")
+    ap.add_argument("--ref-cores", type=int, default=0,
+                    help="host processes of the reference arm (0: every core)")
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--workload", default="mid", choices=["mid", "batched", "served", "ingest"],
+    ap.add_argument("--workload", default="mid", choices=["mid", "batched", "served", "ingest", "resim", "pulse"],
                     help="mid = the headline single-job benchmark; batched / served = the "
                          "multi-job engine against the plain per-job path")
     ap.add_argument("--scale", type=float, default=1.0, help="shrink batched/served workloads")
@@ -428,6 +522,10 @@ def main():
         return run_served_mode(args)
     if args.workload == "ingest":
         return run_ingest_mode(args)
+    if args.workload == "resim":
+        return run_resim_mode(args)
+    if args.workload == "pulse":
+        return run_pulse_mode(args)
     world, rank, local = dist_setup()
     if args.impl == "reference":
         run_reference(args, world, rank)

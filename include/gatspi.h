@@ -95,6 +95,15 @@ typedef struct gatspi_opts {
                             pulse limits the launch shape is 256 threads x 4
                             windows unless tile_items / items_per_thread ask
                             for 256 x 1, 256 x 2 or 128 x 8 (no autotuning) */
+  int32_t first_window;  /* simulate windows [first_window, first_window +
+                            num_windows) only: a segment of a long stimulus
+                            (Section 4: a testbench too long for device
+                            memory runs in shorter segments whose results are
+                            combined).  Window indices and times stay global,
+                            so the SAIF figures (T0, T1, TC) and the digests
+                            of consecutive segments add up to those of the
+                            whole run, and a run can resume at any window */
+  int32_t num_windows;   /* 0 = through the last window */
   int32_t reserved;      /* must be 0 */
 } gatspi_opts;
 

@@ -85,7 +85,8 @@ class gatspi_opts(ctypes.Structure):
                 ("tile_items", ctypes.c_int32), ("time_kernels", ctypes.c_int32),
                 ("items_per_thread", ctypes.c_int32), ("digest", ctypes.c_int32),
                 ("pulse_limits", ctypes.c_int32), ("gate_pulse_percent", ctypes.c_int32),
-                ("wire_pulse_percent", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("wire_pulse_percent", ctypes.c_int32), ("first_window", ctypes.c_int32),
+                ("num_windows", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class gatspi_engine_opts(ctypes.Structure):
@@ -306,12 +307,15 @@ def gatspi_set_stimulus(ctx, num_cycles, cycle_ps, init, edge_ptr, edge_time) ->
 
 
 def gatspi_simulate(ctx, window_cycles=0, batch_windows=0, tile_items=0, time_kernels=0,
-                    items_per_thread=0, digest=0, pulse=None) -> None:
+                    items_per_thread=0, digest=0, pulse=None, first_window=0, num_windows=0) -> None:
     """``pulse``: None for Algorithm 1 as printed, else (gate percent, wire
-    percent), the PATHPULSEPERCENT limits of the two inertial tests."""
+    percent), the PATHPULSEPERCENT limits of the two inertial tests.
+    ``first_window`` / ``num_windows``: a segment of the windows (0 = to the
+    end); segments' SAIF and digests add up to the whole run's."""
     pg, pw = pulse if pulse is not None else (100, 100)
     o = gatspi_opts(int(window_cycles), int(batch_windows), int(tile_items), int(time_kernels),
-                    int(items_per_thread), int(digest), 1 if pulse is not None else 0, int(pg), int(pw))
+                    int(items_per_thread), int(digest), 1 if pulse is not None else 0, int(pg), int(pw),
+                    int(first_window), int(num_windows))
     _check(ctx, lib().gatspi_simulate(ctx, ctypes.byref(o)))
 
 

@@ -10,6 +10,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "gatspi.h"
 #include "host_common.h"
 #include "kernels.cuh"
@@ -21,6 +23,15 @@ using namespace gatspi_dev;
 namespace {
 
 constexpr int64_t kAlign = 256;
+
+// An NVTX range over a host scope (visible in Nsight Systems / Compute
+// timelines; costs nothing when no tool is attached).
+struct nvtx_range {
+  explicit nvtx_range(const char* name) { nvtxRangePushA(name); }
+  ~nvtx_range() { nvtxRangePop(); }
+  nvtx_range(const nvtx_range&) = delete;
+  nvtx_range& operator=(const nvtx_range&) = delete;
+};
 
 int64_t align_up(int64_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
@@ -418,6 +429,7 @@ int gatspi_set_edit(gatspi_ctx* ctx, int32_t n_edits, const int32_t* edit_gate, 
 int gatspi_set_stimulus(gatspi_ctx* ctx, int32_t num_cycles, int32_t cycle_ps, const uint8_t* init,
                         const int64_t* edge_ptr, const int32_t* edge_time) {
   if (!ctx) return GATSPI_EINVAL;
+  nvtx_range range("gatspi_set_stimulus");
   ctx->generation++;
   if (!ctx->have_netlist) return fail(ctx, GATSPI_ESTATE, "load a netlist before the stimulus");
   // the arrays' shape on the host; their contents are checked on the device
@@ -466,6 +478,7 @@ int gatspi_set_stimulus(gatspi_ctx* ctx, int32_t num_cycles, int32_t cycle_ps, c
 int gatspi_set_stimulus_events(gatspi_ctx* ctx, int32_t num_cycles, int32_t cycle_ps, const uint8_t* init,
                                int64_t num_events, const int32_t* ev_input, const int64_t* ev_time) {
   if (!ctx) return GATSPI_EINVAL;
+  nvtx_range range("gatspi_set_stimulus_events");
   ctx->generation++;
   if (!ctx->have_netlist) return fail(ctx, GATSPI_ESTATE, "load a netlist before the stimulus");
   if (num_cycles < 1 || cycle_ps < 1) return fail(ctx, GATSPI_EINVAL, "num_cycles and cycle_ps must be >= 1");
@@ -590,8 +603,15 @@ int simulate_impl(gatspi_ctx* ctx, const gatspi_opts* opts) {
   if (!gatspi_host::horizon_fits(W, ctx->C, ctx->L, ctx->D, ctx->max_gate_delay, ctx->max_wire_delay,
                                  ctx->max_edit))
     return fail(ctx, GATSPI_EINVAL, "window length plus path delays could overflow int32 ps");
-  int32_t n_windows = (ctx->C + W - 1) / W;
-  if (ctx->window_limit > 0) n_windows = std::min(n_windows, ctx->window_limit);
+  // the segment of windows [wb, we) this call simulates
+  const int32_t n_all = (ctx->C + W - 1) / W;
+  if (o.first_window < 0 || o.num_windows < 0 || o.first_window >= n_all)
+    return fail(ctx, GATSPI_EINVAL, "first_window must lie in [0, " + std::to_string(n_all) +
+                                        ") and num_windows must be >= 0");
+  const int32_t wb = o.first_window;
+  int32_t we = o.num_windows ? (int32_t)std::min<int64_t>(n_all, (int64_t)wb + o.num_windows) : n_all;
+  if (ctx->window_limit > 0) we = std::min(we, wb + ctx->window_limit);
+  const int32_t n_windows = we - wb;
   int32_t NW = o.batch_windows ? std::min(o.batch_windows, n_windows) : n_windows;
   // per-level item count must fit int32
   int64_t widest = ctx->I;
@@ -627,10 +647,11 @@ int simulate_impl(gatspi_ctx* ctx, const gatspi_opts* opts) {
   };
   while (NW > 1 && fixed_bytes(ctx, NW, ipt) * 2 > ctx->arena_limit) NW = (NW + 1) / 2;
 
-  int32_t w0 = 0;
+  int32_t w0 = wb;
   int64_t edges_total = 0, rec_bytes = 0;
-  while (w0 < n_windows) {
-    const int32_t nw = std::min(NW, n_windows - w0);
+  while (w0 < we) {
+    nvtx_range batch_range("gatspi batch");
+    const int32_t nw = std::min(NW, we - w0);
     int rc = ensure_arena(ctx, want_bytes(nw));
     if (rc) return rc;
     size_t fixed = 0;
@@ -790,9 +811,9 @@ int simulate_impl(gatspi_ctx* ctx, const gatspi_opts* opts) {
       } else {
         return fail(ctx, GATSPI_ECAPACITY, "waveforms of one window exceed the arena");
       }
-      // restart the whole simulation: SAIF of earlier batches is kept only
-      // if we restart from w0 = 0
-      w0 = 0;
+      // restart the whole segment: SAIF of earlier batches is kept only
+      // if we restart from its first window
+      w0 = wb;
       edges_total = 0;
       rec_bytes = 0;
       first_recorded = false;
@@ -829,7 +850,7 @@ int simulate_impl(gatspi_ctx* ctx, const gatspi_opts* opts) {
   st.windows = n_windows;
   st.batch_windows = NW;
   st.edges = edges_total;
-  ctx->total_time = (int64_t)ctx->C * ctx->L;
+  ctx->total_time = (std::min<int64_t>((int64_t)we * W, ctx->C) - (int64_t)wb * W) * ctx->L;
   // algorithmic bytes: the records' bytes above, plus 4 bytes per edge read
   // by every fanin pin (a pin reads the TC of its driving net) and per edge
   // written by a gate
@@ -899,6 +920,7 @@ extern "C" {
 
 int gatspi_simulate(gatspi_ctx* ctx, const gatspi_opts* opts) {
   if (!ctx) return GATSPI_EINVAL;
+  nvtx_range range("gatspi_simulate");
   if (!ctx->have_netlist || !ctx->have_delays || !ctx->have_stim)
     return fail(ctx, GATSPI_ESTATE, "load a netlist, its delays and a stimulus first");
   gatspi_opts o{};
@@ -925,6 +947,7 @@ int gatspi_simulate(gatspi_ctx* ctx, const gatspi_opts* opts) {
 int gatspi_resimulate_edit(gatspi_ctx* ctx, int32_t n_edits, const int32_t* edit_gate,
                            const int32_t* edit_delta, gatspi_resim_info* info) {
   if (!ctx) return GATSPI_EINVAL;
+  nvtx_range range("gatspi_resimulate_edit");
   if (!ctx->have_last_opts) return fail(ctx, GATSPI_ESTATE, "simulate once before re-simulating an edit");
   if (!ctx->have_netlist || !ctx->have_delays || !ctx->have_stim)
     return fail(ctx, GATSPI_ESTATE, "load a netlist, its delays and a stimulus first");
