@@ -253,7 +253,7 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
-def survey_bytes_per_step(netlist, tc, num_windows):
+def format_bytes_per_step(netlist, tc, num_windows):
     """Algorithmic bytes of one step by the per-(gate, window) figure of the
     paper's waveform format: each fanin waveform read once (a start value,
     an end marker and its edges, 4 bytes each), the output written once
@@ -587,8 +587,8 @@ def main():
     sim.close()
     # the per-unit figure of the waveform format (Holst arrays with start
     # value and end marker) times the step's (gate, cycle) units
-    survey_step = survey_bytes_per_step(wl.netlist, saif[2], C)
-    achieved = survey_step / (statistics.mean(prop_ms) / 1e3) / 1e9
+    format_step = format_bytes_per_step(wl.netlist, saif[2], C)
+    achieved = format_step / (statistics.mean(prop_ms) / 1e3) / 1e9
 
     if rank != 0:
         return
@@ -607,7 +607,7 @@ def main():
                      if WORKLOAD == "mid" and not args.cycles else None,
                      "peak_kind": peak_kind,
                      "kernel": "propagate_kernel",
-                     "algo_bytes_per_step": int(survey_step),
+                     "algo_bytes_per_step": int(format_step),
                      "bytes_per_unit": "4*sum_pins(2+e_pin) + 4*(2+e_out) + 8 per (gate, cycle)",
                      "layout_bytes_per_step": int(algo[-1]),
                      "layout_achieved": layout_achieved, "layout_frac": layout_achieved / peak,
