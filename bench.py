@@ -555,6 +555,8 @@ def main():
     import paper_2203_06117_gb300 as gs
     gs.build()
     device = local
+    import torch
+    torch.cuda.set_device(device)  # pinned staging below belongs to this rank's GPU
     wl = gen.make_workload(WORKLOAD, seed=SEED, num_cycles=args.cycles or None)
     G, C = wl.netlist.num_gates, wl.stim.num_cycles
     units = G * C
