@@ -4,6 +4,8 @@
 // simulator's output for power analysis, Section 3).  Plain C++, no device
 // code; declared in include/gatspi.h.
 #include <cctype>
+#include <climits>
+#include <exception>
 #include <cstdint>
 #include <cstdio>
 #include <cstring>
@@ -56,13 +58,8 @@ int64_t timescale_ps(const std::string& spec) {
   return 0;
 }
 
-}  // namespace
-
-extern "C" {
-
-int gatspi_vcd_read(const char* path, int32_t num_names, const char* const* names, uint8_t* init,
-                    int32_t* ev_input, int64_t* ev_time, int64_t cap, int64_t* num_events, char* err,
-                    int32_t err_len) {
+int vcd_read(const char* path, int32_t num_names, const char* const* names, uint8_t* init, int32_t* ev_input,
+             int64_t* ev_time, int64_t cap, int64_t* num_events, char* err, int32_t err_len) {
   if (!path || num_names < 1 || !names || !init || !num_events || cap < 0 ||
       (cap > 0 && (!ev_input || !ev_time))) {
     say(err, err_len, "bad arguments");
@@ -217,7 +214,15 @@ int gatspi_vcd_read(const char* path, int32_t num_names, const char* const* name
         say(err, err_len, "bad time '" + tok + "'");
         return GATSPI_EINVAL;
       }
+      if (num.size() > 18) {  // keeps the time, and the time in ps, inside int64
+        say(err, err_len, "time too large: '" + tok + "'");
+        return GATSPI_EINVAL;
+      }
       const int64_t t = std::stoll(num);
+      if (t > INT64_MAX / unit_ps) {
+        say(err, err_len, "time too large in ps: '" + tok + "'");
+        return GATSPI_EINVAL;
+      }
       if (have_time && t < now) {
         say(err, err_len, "time goes back at '" + tok + "'");
         return GATSPI_EINVAL;
@@ -269,6 +274,26 @@ int gatspi_vcd_read(const char* path, int32_t num_names, const char* const* name
     return GATSPI_ECAPACITY;
   }
   return GATSPI_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+// The parser reads untrusted files behind a C interface: no exception may
+// leave it.
+int gatspi_vcd_read(const char* path, int32_t num_names, const char* const* names, uint8_t* init,
+                    int32_t* ev_input, int64_t* ev_time, int64_t cap, int64_t* num_events, char* err,
+                    int32_t err_len) {
+  try {
+    return vcd_read(path, num_names, names, init, ev_input, ev_time, cap, num_events, err, err_len);
+  } catch (const std::exception& e) {
+    say(err, err_len, std::string("VCD read failed: ") + e.what());
+    return GATSPI_EINVAL;
+  } catch (...) {
+    say(err, err_len, "VCD read failed");
+    return GATSPI_EINVAL;
+  }
 }
 
 int gatspi_saif_write(const char* path, const char* design, int64_t duration_ps, int32_t num_nets,

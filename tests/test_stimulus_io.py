@@ -190,6 +190,10 @@ BAD_VCDS = {
     "time goes back": "$timescale 1ps $end $var wire 1 ! a $end $enddefinitions $end #0 0! #9 1! #5 0!",
     "fs timescale": "$timescale 100fs $end $var wire 1 ! a $end $enddefinitions $end #0 0!",
     "no enddefinitions": "$timescale 1ps $end $var wire 1 ! a $end #0 0!",
+    "time beyond int64": "$timescale 1ps $end $var wire 1 ! a $end $enddefinitions $end #0 0! "
+                         "#99999999999999999999 1!",
+    "time beyond int64 ps": "$timescale 1s $end $var wire 1 ! a $end $enddefinitions $end #0 0! "
+                            "#100000000 1!",
 }
 
 
