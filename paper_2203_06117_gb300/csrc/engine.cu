@@ -6,6 +6,8 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <exception>
+#include <new>
 #include <chrono>
 #include <cstring>
 #include <deque>
@@ -125,6 +127,20 @@ namespace {
 int efail(gatspi_engine* e, int code, const std::string& msg) {
   if (e) e->err = msg;
   return code;
+}
+
+// As in the single-job interface: no C++ exception crosses the C interface.
+template <class F>
+int guarded(gatspi_engine* e, F&& body) {
+  try {
+    return body();
+  } catch (const std::bad_alloc&) {
+    return efail(e, GATSPI_ENOMEM, "host allocation failed");
+  } catch (const std::exception& x) {
+    return efail(e, GATSPI_EINVAL, std::string("unexpected error: ") + x.what());
+  } catch (...) {
+    return efail(e, GATSPI_EINVAL, "unexpected error");
+  }
 }
 
 #define ECK(call)                                                                        \
@@ -334,92 +350,96 @@ int retire(gatspi_engine* eng, bool wait_one) {
 extern "C" {
 
 int gatspi_engine_create(gatspi_engine** out, int device, size_t arena_bytes, const gatspi_engine_opts* opts) {
-  if (!out) return GATSPI_EINVAL;
-  *out = nullptr;
-  int n = 0;
-  if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) {
-    cudaGetLastError();
-    return GATSPI_EINVAL;
-  }
-  gatspi_engine_opts o{};
-  if (opts) o = *opts;
-  if (o.reserved || o.step_items < 0) return GATSPI_EINVAL;
-  const int nt = o.tile_items ? o.tile_items : 256;
-  const int ipt = o.items_per_thread ? o.items_per_thread : 4;
-  if ((nt != 128 && nt != 256 && nt != 512) || (ipt != 1 && ipt != 2 && ipt != 4 && ipt != 8) ||
-      (nt == 512 && ipt == 8))
-    return GATSPI_EINVAL;
-  if (o.max_active < 0 || o.part_items < 0) return GATSPI_EINVAL;
-  auto* eng = new gatspi_engine();
-  eng->device = device;
-  eng->opts = o;
-  eng->nt = nt;
-  eng->ipt = ipt;
-  eng->tile = tile_items_of(ipt);
-  if (!eng->opts.max_active) eng->opts.max_active = 1024;
-  if (!eng->opts.part_items) eng->opts.part_items = 1ll << 30;
-  if (!eng->opts.step_items) eng->opts.step_items = 1ll << 25;
-  if (cudaSetDevice(device) != cudaSuccess ||
-      cudaStreamCreateWithFlags(&eng->stream, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaStreamCreateWithFlags(&eng->upload, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaMalloc(&eng->d_counter, sizeof(int32_t) * (size_t)(eng->opts.max_active / kMaxSegs + 2)) !=
-          cudaSuccess ||
-      cudaMallocHost(&eng->h_results, sizeof(PartResult) * (size_t)eng->opts.max_active) != cudaSuccess) {
-    cudaGetLastError();
-    gatspi_engine_destroy(eng);
-    return GATSPI_ECUDA;
-  }
-  for (int k = 0; k < gatspi_engine::kRing; ++k)
-    if (cudaEventCreateWithFlags(&eng->stage_ev[k], cudaEventDisableTiming) != cudaSuccess) {
+  return guarded(nullptr, [&]() -> int {
+    if (!out) return GATSPI_EINVAL;
+    *out = nullptr;
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) {
+      cudaGetLastError();
+      return GATSPI_EINVAL;
+    }
+    gatspi_engine_opts o{};
+    if (opts) o = *opts;
+    if (o.reserved || o.step_items < 0) return GATSPI_EINVAL;
+    const int nt = o.tile_items ? o.tile_items : 256;
+    const int ipt = o.items_per_thread ? o.items_per_thread : 4;
+    if ((nt != 128 && nt != 256 && nt != 512) || (ipt != 1 && ipt != 2 && ipt != 4 && ipt != 8) ||
+        (nt == 512 && ipt == 8))
+      return GATSPI_EINVAL;
+    if (o.max_active < 0 || o.part_items < 0) return GATSPI_EINVAL;
+    auto* eng = new gatspi_engine();
+    eng->device = device;
+    eng->opts = o;
+    eng->nt = nt;
+    eng->ipt = ipt;
+    eng->tile = tile_items_of(ipt);
+    if (!eng->opts.max_active) eng->opts.max_active = 1024;
+    if (!eng->opts.part_items) eng->opts.part_items = 1ll << 30;
+    if (!eng->opts.step_items) eng->opts.step_items = 1ll << 25;
+    if (cudaSetDevice(device) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&eng->stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&eng->upload, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaMalloc(&eng->d_counter, sizeof(int32_t) * (size_t)(eng->opts.max_active / kMaxSegs + 2)) !=
+            cudaSuccess ||
+        cudaMallocHost(&eng->h_results, sizeof(PartResult) * (size_t)eng->opts.max_active) != cudaSuccess) {
+      cudaGetLastError();
       gatspi_engine_destroy(eng);
       return GATSPI_ECUDA;
     }
-  for (int32_t s = eng->opts.max_active - 1; s >= 0; --s) eng->free_slots.push_back(s);
-  // keep freed part memory in the device pool between steps
-  cudaMemPool_t pool;
-  if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
-    uint64_t thr = ~0ull;
-    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
-  }
-  size_t free_b = 0, total_b = 0;
-  cudaMemGetInfo(&free_b, &total_b);
-  eng->budget = arena_bytes ? arena_bytes : (size_t)(0.85 * (double)free_b);
-  *out = eng;
-  return GATSPI_OK;
+    for (int k = 0; k < gatspi_engine::kRing; ++k)
+      if (cudaEventCreateWithFlags(&eng->stage_ev[k], cudaEventDisableTiming) != cudaSuccess) {
+        gatspi_engine_destroy(eng);
+        return GATSPI_ECUDA;
+      }
+    for (int32_t s = eng->opts.max_active - 1; s >= 0; --s) eng->free_slots.push_back(s);
+    // keep freed part memory in the device pool between steps
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
+      uint64_t thr = ~0ull;
+      cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    size_t free_b = 0, total_b = 0;
+    cudaMemGetInfo(&free_b, &total_b);
+    eng->budget = arena_bytes ? arena_bytes : (size_t)(0.85 * (double)free_b);
+    *out = eng;
+    return GATSPI_OK;
+  });
 }
 
 int gatspi_engine_destroy(gatspi_engine* eng) {
-  if (!eng) return GATSPI_OK;
-  cudaSetDevice(eng->device);
-  if (eng->stream) cudaStreamSynchronize(eng->stream);
-  auto drop = [&](std::unique_ptr<EPart>& p) {
-    if (p->mem) cudaFree(p->mem);
-    if (p->ev) cudaEventDestroy(p->ev);
-  };
-  for (auto& p : eng->active) drop(p);
-  for (auto& p : eng->finishing) drop(p);
-  for (auto& kv : eng->jobs) free_job_device(*kv.second, eng->stream);
-  if (eng->stream) cudaStreamSynchronize(eng->stream);
-  for (auto& nl : eng->nets) {
-    dfree(nl->d_fanin_ptr); dfree(nl->d_fanin_net); dfree(nl->d_net_level); dfree(nl->d_gate_desc);
-    dfree(nl->d_gate_delay); dfree(nl->d_wire_delay); dfree(nl->d_lut);
-  }
-  for (int k = 0; k < gatspi_engine::kRing; ++k) {
-    if (eng->h_stage[k]) cudaFreeHost(eng->h_stage[k]);
-    if (eng->stage_ev[k]) cudaEventDestroy(eng->stage_ev[k]);
-  }
-  for (auto e : eng->free_events) cudaEventDestroy(e);
-  dfree(eng->d_stage);
-  dfree(eng->d_counter);
-  if (eng->h_results) cudaFreeHost(eng->h_results);
-  if (eng->upload) cudaStreamSynchronize(eng->upload);
-  if (eng->upload) cudaStreamDestroy(eng->upload);
-  if (eng->stream) cudaStreamDestroy(eng->stream);
-  // hand the memory parked in the stream-ordered pool back to the device
-  cudaMemPool_t pool;
-  if (cudaDeviceGetDefaultMemPool(&pool, eng->device) == cudaSuccess) cudaMemPoolTrimTo(pool, 0);
-  delete eng;
-  return GATSPI_OK;
+  return guarded(eng, [&]() -> int {
+    if (!eng) return GATSPI_OK;
+    cudaSetDevice(eng->device);
+    if (eng->stream) cudaStreamSynchronize(eng->stream);
+    auto drop = [&](std::unique_ptr<EPart>& p) {
+      if (p->mem) cudaFree(p->mem);
+      if (p->ev) cudaEventDestroy(p->ev);
+    };
+    for (auto& p : eng->active) drop(p);
+    for (auto& p : eng->finishing) drop(p);
+    for (auto& kv : eng->jobs) free_job_device(*kv.second, eng->stream);
+    if (eng->stream) cudaStreamSynchronize(eng->stream);
+    for (auto& nl : eng->nets) {
+      dfree(nl->d_fanin_ptr); dfree(nl->d_fanin_net); dfree(nl->d_net_level); dfree(nl->d_gate_desc);
+      dfree(nl->d_gate_delay); dfree(nl->d_wire_delay); dfree(nl->d_lut);
+    }
+    for (int k = 0; k < gatspi_engine::kRing; ++k) {
+      if (eng->h_stage[k]) cudaFreeHost(eng->h_stage[k]);
+      if (eng->stage_ev[k]) cudaEventDestroy(eng->stage_ev[k]);
+    }
+    for (auto e : eng->free_events) cudaEventDestroy(e);
+    dfree(eng->d_stage);
+    dfree(eng->d_counter);
+    if (eng->h_results) cudaFreeHost(eng->h_results);
+    if (eng->upload) cudaStreamSynchronize(eng->upload);
+    if (eng->upload) cudaStreamDestroy(eng->upload);
+    if (eng->stream) cudaStreamDestroy(eng->stream);
+    // hand the memory parked in the stream-ordered pool back to the device
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, eng->device) == cudaSuccess) cudaMemPoolTrimTo(pool, 0);
+    delete eng;
+    return GATSPI_OK;
+  });
 }
 
 const char* gatspi_engine_last_error(gatspi_engine* eng) { return eng ? eng->err.c_str() : "null engine"; }
@@ -427,98 +447,102 @@ const char* gatspi_engine_last_error(gatspi_engine* eng) { return eng ? eng->err
 int gatspi_engine_add_netlist(gatspi_engine* eng, int32_t num_inputs, int32_t num_gates,
                               const int32_t* fanin_ptr, const int32_t* fanin_net, const uint16_t* lut,
                               const int32_t* gate_delay, const int32_t* wire_delay, int32_t* netlist_id) {
-  if (!eng || !netlist_id) return GATSPI_EINVAL;
-  std::unique_ptr<ENetlist> nl(new ENetlist());
-  std::string why = gatspi_host::prepare_netlist(num_inputs, num_gates, fanin_ptr, fanin_net, lut, &nl->r);
-  if (!why.empty()) return efail(eng, GATSPI_EINVAL, why);
-  std::vector<int32_t> gd, wd;
-  why = gatspi_host::prepare_delays(nl->r, gate_delay, wire_delay, &gd, &wd, &nl->max_gate, &nl->max_wire);
-  if (!why.empty()) return efail(eng, GATSPI_EINVAL, why);
-  ECK(cudaSetDevice(eng->device));
-  int rc;
-  if ((rc = eupload(eng, nl->d_fanin_ptr, nl->r.fanin_ptr.data(), nl->r.fanin_ptr.size()))) return rc;
-  if ((rc = eupload(eng, nl->d_fanin_net, nl->r.fanin_net.data(), nl->r.fanin_net.size()))) return rc;
-  if ((rc = eupload(eng, nl->d_net_level, nl->r.net_level.data(), nl->r.net_level.size()))) return rc;
-  if ((rc = eupload(eng, nl->d_lut, nl->r.lut.data(), nl->r.lut.size()))) return rc;
-  if (!nl->r.gate_desc.empty() &&
-      (rc = eupload(eng, nl->d_gate_desc, nl->r.gate_desc.data(), nl->r.gate_desc.size())))
-    return rc;
-  if ((rc = eupload(eng, nl->d_gate_delay, gd.data(), gd.size()))) return rc;
-  if ((rc = eupload(eng, nl->d_wire_delay, wd.data(), wd.size()))) return rc;
-  *netlist_id = (int32_t)eng->nets.size();
-  eng->nets.push_back(std::move(nl));
-  return GATSPI_OK;
+  return guarded(eng, [&]() -> int {
+    if (!eng || !netlist_id) return GATSPI_EINVAL;
+    std::unique_ptr<ENetlist> nl(new ENetlist());
+    std::string why = gatspi_host::prepare_netlist(num_inputs, num_gates, fanin_ptr, fanin_net, lut, &nl->r);
+    if (!why.empty()) return efail(eng, GATSPI_EINVAL, why);
+    std::vector<int32_t> gd, wd;
+    why = gatspi_host::prepare_delays(nl->r, gate_delay, wire_delay, &gd, &wd, &nl->max_gate, &nl->max_wire);
+    if (!why.empty()) return efail(eng, GATSPI_EINVAL, why);
+    ECK(cudaSetDevice(eng->device));
+    int rc;
+    if ((rc = eupload(eng, nl->d_fanin_ptr, nl->r.fanin_ptr.data(), nl->r.fanin_ptr.size()))) return rc;
+    if ((rc = eupload(eng, nl->d_fanin_net, nl->r.fanin_net.data(), nl->r.fanin_net.size()))) return rc;
+    if ((rc = eupload(eng, nl->d_net_level, nl->r.net_level.data(), nl->r.net_level.size()))) return rc;
+    if ((rc = eupload(eng, nl->d_lut, nl->r.lut.data(), nl->r.lut.size()))) return rc;
+    if (!nl->r.gate_desc.empty() &&
+        (rc = eupload(eng, nl->d_gate_desc, nl->r.gate_desc.data(), nl->r.gate_desc.size())))
+      return rc;
+    if ((rc = eupload(eng, nl->d_gate_delay, gd.data(), gd.size()))) return rc;
+    if ((rc = eupload(eng, nl->d_wire_delay, wd.data(), wd.size()))) return rc;
+    *netlist_id = (int32_t)eng->nets.size();
+    eng->nets.push_back(std::move(nl));
+    return GATSPI_OK;
+  });
 }
 
 int gatspi_engine_submit(gatspi_engine* eng, int32_t netlist_id, int32_t num_cycles, int32_t cycle_ps,
                          const uint8_t* init, const int64_t* edge_ptr, const int32_t* edge_time,
                          int32_t window_cycles, int32_t n_edits, const int32_t* edit_gate,
                          const int32_t* edit_delta, int64_t* job_id) {
-  if (!eng || !job_id) return GATSPI_EINVAL;
-  if (netlist_id < 0 || netlist_id >= (int32_t)eng->nets.size())
-    return efail(eng, GATSPI_EINVAL, "unknown netlist id");
-  ENetlist& nl = *eng->nets[netlist_id];
-  std::string why = gatspi_host::validate_stimulus(nl.r.I, num_cycles, cycle_ps, init, edge_ptr, edge_time);
-  if (!why.empty()) return efail(eng, GATSPI_EINVAL, why);
-  const int32_t W = window_cycles ? window_cycles : 1;
-  if (W < 1) return efail(eng, GATSPI_EINVAL, "window_cycles must be >= 1");
-  if (n_edits < 0 || (n_edits > 0 && (!edit_gate || !edit_delta)))
-    return efail(eng, GATSPI_EINVAL, "bad delay edit arrays");
-  std::vector<int32_t> delta;
-  int32_t max_edit = 0;
-  if (n_edits > 0) {
-    delta.assign(nl.r.G, 0);
-    for (int32_t k = 0; k < n_edits; ++k) {
-      const int32_t g = edit_gate[k];
-      if (g < 0 || g >= nl.r.G) return efail(eng, GATSPI_EINVAL, "edit names an unknown gate");
-      if (edit_delta[k] < -gatspi_host::kMaxDelay || edit_delta[k] > gatspi_host::kMaxDelay)
-        return efail(eng, GATSPI_EINVAL, "edit delta outside +-2^24 ps");
-      delta[nl.r.gate_int[g]] = edit_delta[k];
-      max_edit = std::max(max_edit, edit_delta[k]);
+  return guarded(eng, [&]() -> int {
+    if (!eng || !job_id) return GATSPI_EINVAL;
+    if (netlist_id < 0 || netlist_id >= (int32_t)eng->nets.size())
+      return efail(eng, GATSPI_EINVAL, "unknown netlist id");
+    ENetlist& nl = *eng->nets[netlist_id];
+    std::string why = gatspi_host::validate_stimulus(nl.r.I, num_cycles, cycle_ps, init, edge_ptr, edge_time);
+    if (!why.empty()) return efail(eng, GATSPI_EINVAL, why);
+    const int32_t W = window_cycles ? window_cycles : 1;
+    if (W < 1) return efail(eng, GATSPI_EINVAL, "window_cycles must be >= 1");
+    if (n_edits < 0 || (n_edits > 0 && (!edit_gate || !edit_delta)))
+      return efail(eng, GATSPI_EINVAL, "bad delay edit arrays");
+    std::vector<int32_t> delta;
+    int32_t max_edit = 0;
+    if (n_edits > 0) {
+      delta.assign(nl.r.G, 0);
+      for (int32_t k = 0; k < n_edits; ++k) {
+        const int32_t g = edit_gate[k];
+        if (g < 0 || g >= nl.r.G) return efail(eng, GATSPI_EINVAL, "edit names an unknown gate");
+        if (edit_delta[k] < -gatspi_host::kMaxDelay || edit_delta[k] > gatspi_host::kMaxDelay)
+          return efail(eng, GATSPI_EINVAL, "edit delta outside +-2^24 ps");
+        delta[nl.r.gate_int[g]] = edit_delta[k];
+        max_edit = std::max(max_edit, edit_delta[k]);
+      }
     }
-  }
-  if (!gatspi_host::horizon_fits(W, num_cycles, cycle_ps, nl.r.D, nl.max_gate, nl.max_wire, max_edit))
-    return efail(eng, GATSPI_EINVAL, "window length plus path delays could overflow int32 ps");
-  ECK(cudaSetDevice(eng->device));
-  std::unique_ptr<EJob> j(new EJob());
-  j->id = eng->next_job++;
-  j->net = netlist_id;
-  j->C = num_cycles; j->L = cycle_ps; j->W = W; j->max_edit = max_edit;
-  j->n_windows = (num_cycles + W - 1) / W;
-  const int64_t n = (int64_t)nl.r.I * num_cycles;
-  j->edge_ptr.assign(edge_ptr, edge_ptr + n + 1);
-  int rc;
-  auto undo = [&](int code) { free_job_device(*j, eng->stream); return code; };
-  if ((rc = eupload_async(eng, j->d_edge_ptr, edge_ptr, (size_t)n + 1))) return undo(rc);
-  if ((rc = eupload_async(eng, j->d_edge_time, edge_time, (size_t)edge_ptr[n]))) return undo(rc);
-  if ((rc = eupload_async(eng, j->d_init_in, init, (size_t)nl.r.I))) return undo(rc);
-  if (n_edits > 0 && (rc = eupload_async(eng, j->d_gate_delta, delta.data(), delta.size()))) return undo(rc);
-  if ((rc = eupload_async<unsigned long long>(eng, j->d_t1, nullptr, nl.r.N))) return undo(rc);
-  if ((rc = eupload_async<unsigned long long>(eng, j->d_tc, nullptr, nl.r.N))) return undo(rc);
-  ECK(cudaMemsetAsync(j->d_t1, 0, sizeof(unsigned long long) * nl.r.N, eng->upload));
-  ECK(cudaMemsetAsync(j->d_tc, 0, sizeof(unsigned long long) * nl.r.N, eng->upload));
-  ECK(cudaEventCreateWithFlags(&j->ready_ev, cudaEventDisableTiming));
-  ECK(cudaEventRecord(j->ready_ev, eng->upload));
-  // cut into parts of at most part_items (gate, window) items and a level
-  // item count that fits int32
-  int64_t widest = nl.r.I;
-  for (int32_t l = 1; l <= nl.r.D; ++l)
-    widest = std::max<int64_t>(widest, nl.r.lvl_gate_begin[l + 1] - nl.r.lvl_gate_begin[l]);
-  int64_t per = std::max<int64_t>(1, eng->opts.part_items / std::max<int64_t>(nl.r.N, 1));
-  per = std::min<int64_t>(per, 0x7fff0000ll / widest);
-  per = std::max<int64_t>(per, 1);
-  for (int32_t w0 = 0; w0 < j->n_windows; w0 += (int32_t)per) {
-    std::unique_ptr<EPart> p(new EPart());
-    p->job = j->id;
-    p->D = nl.r.D;
-    p->w0 = w0;
-    p->nw = (int32_t)std::min<int64_t>(per, j->n_windows - w0);
-    eng->queued.push_back(std::move(p));
-    j->parts_total++;
-  }
-  *job_id = j->id;
-  eng->jobs[j->id] = std::move(j);
-  return GATSPI_OK;
+    if (!gatspi_host::horizon_fits(W, num_cycles, cycle_ps, nl.r.D, nl.max_gate, nl.max_wire, max_edit))
+      return efail(eng, GATSPI_EINVAL, "window length plus path delays could overflow int32 ps");
+    ECK(cudaSetDevice(eng->device));
+    std::unique_ptr<EJob> j(new EJob());
+    j->id = eng->next_job++;
+    j->net = netlist_id;
+    j->C = num_cycles; j->L = cycle_ps; j->W = W; j->max_edit = max_edit;
+    j->n_windows = (num_cycles + W - 1) / W;
+    const int64_t n = (int64_t)nl.r.I * num_cycles;
+    j->edge_ptr.assign(edge_ptr, edge_ptr + n + 1);
+    int rc;
+    auto undo = [&](int code) { free_job_device(*j, eng->stream); return code; };
+    if ((rc = eupload_async(eng, j->d_edge_ptr, edge_ptr, (size_t)n + 1))) return undo(rc);
+    if ((rc = eupload_async(eng, j->d_edge_time, edge_time, (size_t)edge_ptr[n]))) return undo(rc);
+    if ((rc = eupload_async(eng, j->d_init_in, init, (size_t)nl.r.I))) return undo(rc);
+    if (n_edits > 0 && (rc = eupload_async(eng, j->d_gate_delta, delta.data(), delta.size()))) return undo(rc);
+    if ((rc = eupload_async<unsigned long long>(eng, j->d_t1, nullptr, nl.r.N))) return undo(rc);
+    if ((rc = eupload_async<unsigned long long>(eng, j->d_tc, nullptr, nl.r.N))) return undo(rc);
+    ECK(cudaMemsetAsync(j->d_t1, 0, sizeof(unsigned long long) * nl.r.N, eng->upload));
+    ECK(cudaMemsetAsync(j->d_tc, 0, sizeof(unsigned long long) * nl.r.N, eng->upload));
+    ECK(cudaEventCreateWithFlags(&j->ready_ev, cudaEventDisableTiming));
+    ECK(cudaEventRecord(j->ready_ev, eng->upload));
+    // cut into parts of at most part_items (gate, window) items and a level
+    // item count that fits int32
+    int64_t widest = nl.r.I;
+    for (int32_t l = 1; l <= nl.r.D; ++l)
+      widest = std::max<int64_t>(widest, nl.r.lvl_gate_begin[l + 1] - nl.r.lvl_gate_begin[l]);
+    int64_t per = std::max<int64_t>(1, eng->opts.part_items / std::max<int64_t>(nl.r.N, 1));
+    per = std::min<int64_t>(per, 0x7fff0000ll / widest);
+    per = std::max<int64_t>(per, 1);
+    for (int32_t w0 = 0; w0 < j->n_windows; w0 += (int32_t)per) {
+      std::unique_ptr<EPart> p(new EPart());
+      p->job = j->id;
+      p->D = nl.r.D;
+      p->w0 = w0;
+      p->nw = (int32_t)std::min<int64_t>(per, j->n_windows - w0);
+      eng->queued.push_back(std::move(p));
+      j->parts_total++;
+    }
+    *job_id = j->id;
+    eng->jobs[j->id] = std::move(j);
+    return GATSPI_OK;
+  });
 }
 
 static int engine_step_impl(gatspi_engine* eng, int32_t* active_out, int32_t* queued_out) {
@@ -733,79 +757,89 @@ static int engine_step_impl(gatspi_engine* eng, int32_t* active_out, int32_t* qu
 }
 
 int gatspi_engine_step(gatspi_engine* eng, int32_t* active_out, int32_t* queued_out) {
-  if (!eng) return GATSPI_EINVAL;
-  const auto t = std::chrono::steady_clock::now();
-  const int rc = engine_step_impl(eng, active_out, queued_out);
-  eng->stats.host_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t).count();
-  return rc;
+  return guarded(eng, [&]() -> int {
+    if (!eng) return GATSPI_EINVAL;
+    const auto t = std::chrono::steady_clock::now();
+    const int rc = engine_step_impl(eng, active_out, queued_out);
+    eng->stats.host_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t).count();
+    return rc;
+  });
 }
 
 int gatspi_engine_drain(gatspi_engine* eng) {
-  if (!eng) return GATSPI_EINVAL;
-  int rc = GATSPI_OK;
-  for (;;) {
-    int32_t a = 0, q = 0;
-    const int r = gatspi_engine_step(eng, &a, &q);
-    if (r && !rc) rc = r;
-    if (r == GATSPI_ECUDA) return r;
-    if (a == 0 && q == 0) break;
-  }
-  ECK(cudaStreamSynchronize(eng->stream));
-  return rc;
+  return guarded(eng, [&]() -> int {
+    if (!eng) return GATSPI_EINVAL;
+    int rc = GATSPI_OK;
+    for (;;) {
+      int32_t a = 0, q = 0;
+      const int r = gatspi_engine_step(eng, &a, &q);
+      if (r && !rc) rc = r;
+      if (r == GATSPI_ECUDA) return r;
+      if (a == 0 && q == 0) break;
+    }
+    ECK(cudaStreamSynchronize(eng->stream));
+    return rc;
+  });
 }
 
 int gatspi_engine_poll(gatspi_engine* eng, int64_t job_id, int32_t* state, int64_t* t0, int64_t* t1,
                        int64_t* tc) {
-  if (!eng) return GATSPI_EINVAL;
-  auto it = eng->jobs.find(job_id);
-  if (it == eng->jobs.end()) return efail(eng, GATSPI_EINVAL, "unknown job id");
-  EJob& j = *it->second;
-  ECK(cudaSetDevice(eng->device));
-  if (j.state != GATSPI_JOB_FAILED && j.done_recorded) {
-    const cudaError_t q = cudaEventQuery(j.done_ev);
-    if (q == cudaSuccess) j.state = GATSPI_JOB_DONE;
-    else if (q != cudaErrorNotReady) return efail(eng, GATSPI_ECUDA, cudaGetErrorString(q));
-  }
-  if (state) *state = j.state;
-  if (j.state == GATSPI_JOB_DONE && (t0 || t1 || tc)) {
-    const ENetlist& nl = *eng->nets[j.net];
-    const int32_t N = nl.r.N;
-    std::vector<unsigned long long> a(N), b(N);
-    ECK(cudaMemcpy(a.data(), j.d_t1, sizeof(unsigned long long) * N, cudaMemcpyDeviceToHost));
-    ECK(cudaMemcpy(b.data(), j.d_tc, sizeof(unsigned long long) * N, cudaMemcpyDeviceToHost));
-    const int64_t total = (int64_t)j.C * j.L;
-    for (int32_t e = 0; e < N; ++e) {
-      const int32_t n = nl.r.net_int[e];
-      if (t1) t1[e] = (int64_t)a[n];
-      if (t0) t0[e] = total - (int64_t)a[n];
-      if (tc) tc[e] = (int64_t)b[n];
+  return guarded(eng, [&]() -> int {
+    if (!eng) return GATSPI_EINVAL;
+    auto it = eng->jobs.find(job_id);
+    if (it == eng->jobs.end()) return efail(eng, GATSPI_EINVAL, "unknown job id");
+    EJob& j = *it->second;
+    ECK(cudaSetDevice(eng->device));
+    if (j.state != GATSPI_JOB_FAILED && j.done_recorded) {
+      const cudaError_t q = cudaEventQuery(j.done_ev);
+      if (q == cudaSuccess) j.state = GATSPI_JOB_DONE;
+      else if (q != cudaErrorNotReady) return efail(eng, GATSPI_ECUDA, cudaGetErrorString(q));
     }
-  }
-  if (j.state == GATSPI_JOB_FAILED) return efail(eng, GATSPI_OK, j.err);
-  return GATSPI_OK;
+    if (state) *state = j.state;
+    if (j.state == GATSPI_JOB_DONE && (t0 || t1 || tc)) {
+      const ENetlist& nl = *eng->nets[j.net];
+      const int32_t N = nl.r.N;
+      std::vector<unsigned long long> a(N), b(N);
+      ECK(cudaMemcpy(a.data(), j.d_t1, sizeof(unsigned long long) * N, cudaMemcpyDeviceToHost));
+      ECK(cudaMemcpy(b.data(), j.d_tc, sizeof(unsigned long long) * N, cudaMemcpyDeviceToHost));
+      const int64_t total = (int64_t)j.C * j.L;
+      for (int32_t e = 0; e < N; ++e) {
+        const int32_t n = nl.r.net_int[e];
+        if (t1) t1[e] = (int64_t)a[n];
+        if (t0) t0[e] = total - (int64_t)a[n];
+        if (tc) tc[e] = (int64_t)b[n];
+      }
+    }
+    if (j.state == GATSPI_JOB_FAILED) return efail(eng, GATSPI_OK, j.err);
+    return GATSPI_OK;
+  });
 }
 
 int gatspi_engine_release(gatspi_engine* eng, int64_t job_id) {
-  if (!eng) return GATSPI_EINVAL;
-  auto it = eng->jobs.find(job_id);
-  if (it == eng->jobs.end()) return efail(eng, GATSPI_EINVAL, "unknown job id");
-  EJob& j = *it->second;
-  if (j.state != GATSPI_JOB_DONE && j.state != GATSPI_JOB_FAILED)
-    return efail(eng, GATSPI_ESTATE, "job still running");
-  for (auto& p : eng->active)
-    if (p->job == job_id) return efail(eng, GATSPI_ESTATE, "job still has parts in flight");
-  for (auto& p : eng->finishing)
-    if (p->job == job_id) return efail(eng, GATSPI_ESTATE, "job still has parts in flight");
-  ECK(cudaSetDevice(eng->device));
-  free_job_device(j, eng->stream);
-  eng->jobs.erase(it);
-  return GATSPI_OK;
+  return guarded(eng, [&]() -> int {
+    if (!eng) return GATSPI_EINVAL;
+    auto it = eng->jobs.find(job_id);
+    if (it == eng->jobs.end()) return efail(eng, GATSPI_EINVAL, "unknown job id");
+    EJob& j = *it->second;
+    if (j.state != GATSPI_JOB_DONE && j.state != GATSPI_JOB_FAILED)
+      return efail(eng, GATSPI_ESTATE, "job still running");
+    for (auto& p : eng->active)
+      if (p->job == job_id) return efail(eng, GATSPI_ESTATE, "job still has parts in flight");
+    for (auto& p : eng->finishing)
+      if (p->job == job_id) return efail(eng, GATSPI_ESTATE, "job still has parts in flight");
+    ECK(cudaSetDevice(eng->device));
+    free_job_device(j, eng->stream);
+    eng->jobs.erase(it);
+    return GATSPI_OK;
+  });
 }
 
 int gatspi_engine_get_stats(gatspi_engine* eng, gatspi_engine_stats* out) {
-  if (!eng || !out) return GATSPI_EINVAL;
-  *out = eng->stats;
-  return GATSPI_OK;
+  return guarded(eng, [&]() -> int {
+    if (!eng || !out) return GATSPI_EINVAL;
+    *out = eng->stats;
+    return GATSPI_OK;
+  });
 }
 
 }  // extern "C"

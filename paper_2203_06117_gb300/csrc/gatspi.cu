@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <exception>
+#include <new>
 #include <chrono>
 #include <cstdio>
 #include <cstring>
@@ -137,6 +139,22 @@ namespace {
 int fail(gatspi_ctx* c, int code, const std::string& msg) {
   if (c) c->err = msg;
   return code;
+}
+
+// Entry points run their bodies through this: a C++ exception (a host
+// allocation sized by the caller's input, a string operation) must not
+// cross the C interface; it becomes a status and a message instead.
+template <class F>
+int guarded(gatspi_ctx* c, F&& body) {
+  try {
+    return body();
+  } catch (const std::bad_alloc&) {
+    return fail(c, GATSPI_ENOMEM, "host allocation failed");
+  } catch (const std::exception& e) {
+    return fail(c, GATSPI_EINVAL, std::string("unexpected error: ") + e.what());
+  } catch (...) {
+    return fail(c, GATSPI_EINVAL, "unexpected error");
+  }
 }
 
 #define CK(call)                                                                      \
@@ -296,258 +314,272 @@ int apply_edit(gatspi_ctx* ctx, std::vector<int32_t> delta) {
 extern "C" {
 
 int gatspi_create(gatspi_ctx** out, int device, size_t arena_bytes) {
-  gatspi_ctx* ctx = nullptr;
-  if (!out) return GATSPI_EINVAL;
-  *out = nullptr;
-  int n = 0;
-  if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) {
-    cudaGetLastError();
-    return GATSPI_EINVAL;
-  }
-  ctx = new gatspi_ctx();
-  ctx->device = device;
-  if (cudaSetDevice(device) != cudaSuccess ||
-      cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaMalloc(&ctx->d_status, sizeof(int32_t)) != cudaSuccess ||
-      cudaMallocHost(&ctx->h_ret, 2 * sizeof(long long)) != cudaSuccess) {
-    cudaGetLastError();
-    delete ctx;
-    return GATSPI_ECUDA;
-  }
-  size_t free_b = 0, total_b = 0;
-  cudaMemGetInfo(&free_b, &total_b);
-  ctx->arena_limit = arena_bytes ? arena_bytes : (size_t)(0.85 * (double)free_b);
-  *out = ctx;
-  return GATSPI_OK;
+  return guarded(nullptr, [&]() -> int {
+    gatspi_ctx* ctx = nullptr;
+    if (!out) return GATSPI_EINVAL;
+    *out = nullptr;
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) {
+      cudaGetLastError();
+      return GATSPI_EINVAL;
+    }
+    ctx = new gatspi_ctx();
+    ctx->device = device;
+    if (cudaSetDevice(device) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaMalloc(&ctx->d_status, sizeof(int32_t)) != cudaSuccess ||
+        cudaMallocHost(&ctx->h_ret, 2 * sizeof(long long)) != cudaSuccess) {
+      cudaGetLastError();
+      delete ctx;
+      return GATSPI_ECUDA;
+    }
+    size_t free_b = 0, total_b = 0;
+    cudaMemGetInfo(&free_b, &total_b);
+    ctx->arena_limit = arena_bytes ? arena_bytes : (size_t)(0.85 * (double)free_b);
+    *out = ctx;
+    return GATSPI_OK;
+  });
 }
 
 int gatspi_destroy(gatspi_ctx* ctx) {
-  if (!ctx) return GATSPI_OK;
-  cudaSetDevice(ctx->device);
-  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
-  free_netlist(ctx);
-  free_stim(ctx);
-  free_arena(ctx);
-  dfree(ctx->d_status);
-  dfree(ctx->d_append);
-  if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
-  if (ctx->h_in_prefix) cudaFreeHost(ctx->h_in_prefix);
-  if (ctx->h_bounds) cudaFreeHost(ctx->h_bounds);
-  if (ctx->h_ret) cudaFreeHost(ctx->h_ret);
-  dfree(ctx->d_first_bad);
-  for (auto e : ctx->ev) cudaEventDestroy(e);
-  if (ctx->stream) cudaStreamDestroy(ctx->stream);
-  delete ctx;
-  return GATSPI_OK;
+  return guarded(ctx, [&]() -> int {
+    if (!ctx) return GATSPI_OK;
+    cudaSetDevice(ctx->device);
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    free_netlist(ctx);
+    free_stim(ctx);
+    free_arena(ctx);
+    dfree(ctx->d_status);
+    dfree(ctx->d_append);
+    if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
+    if (ctx->h_in_prefix) cudaFreeHost(ctx->h_in_prefix);
+    if (ctx->h_bounds) cudaFreeHost(ctx->h_bounds);
+    if (ctx->h_ret) cudaFreeHost(ctx->h_ret);
+    dfree(ctx->d_first_bad);
+    for (auto e : ctx->ev) cudaEventDestroy(e);
+    if (ctx->stream) cudaStreamDestroy(ctx->stream);
+    delete ctx;
+    return GATSPI_OK;
+  });
 }
 
 const char* gatspi_last_error(gatspi_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
 
 int gatspi_load_netlist(gatspi_ctx* ctx, int32_t num_inputs, int32_t num_gates,
                         const int32_t* fanin_ptr, const int32_t* fanin_net, const uint16_t* lut) {
-  if (!ctx) return GATSPI_EINVAL;
-  ctx->generation++;
-  gatspi_host::Prepared r;
-  const std::string why = gatspi_host::prepare_netlist(num_inputs, num_gates, fanin_ptr, fanin_net, lut, &r);
-  if (!why.empty()) return fail(ctx, GATSPI_EINVAL, why);
-  CK(cudaSetDevice(ctx->device));
-  ctx->have_netlist = ctx->have_delays = ctx->have_stim = ctx->have_result = false;
-  ctx->tuned_nt = ctx->tuned_ipt = 0;
-  free_netlist(ctx);
-  ctx->I = r.I; ctx->G = r.G; ctx->N = r.N; ctx->P = r.P; ctx->D = r.D;
-  ctx->gate_ext = std::move(r.gate_ext);
-  ctx->net_int = std::move(r.net_int);
-  ctx->pin_ext = std::move(r.pin_ext);
-  ctx->fanin_ptr = std::move(r.fanin_ptr);
-  ctx->fanin_net = std::move(r.fanin_net);
-  ctx->net_level = std::move(r.net_level);
-  ctx->lut = std::move(r.lut);
-  ctx->lvl_gate_begin = std::move(r.lvl_gate_begin);
-  ctx->fanout = std::move(r.fanout);
-  int rc;
-  if (!r.gate_desc.empty()) {
-    if ((rc = upload(ctx, ctx->d_gate_desc, r.gate_desc.data(), r.gate_desc.size()))) return rc;
-  } else {
-    dfree(ctx->d_gate_desc);
-  }
-  if ((rc = upload(ctx, ctx->d_fanin_ptr, ctx->fanin_ptr.data(), ctx->fanin_ptr.size()))) return rc;
-  if ((rc = upload(ctx, ctx->d_fanin_net, ctx->fanin_net.data(), ctx->fanin_net.size()))) return rc;
-  if ((rc = upload(ctx, ctx->d_net_level, ctx->net_level.data(), ctx->net_level.size()))) return rc;
-  if ((rc = upload(ctx, ctx->d_lut, ctx->lut.data(), ctx->lut.size()))) return rc;
-  if ((rc = upload<unsigned long long>(ctx, ctx->d_t1, nullptr, ctx->N))) return rc;
-  if ((rc = upload<unsigned long long>(ctx, ctx->d_tc, nullptr, ctx->N))) return rc;
-  if ((rc = upload<unsigned long long>(ctx, ctx->d_digest, nullptr, ctx->N))) return rc;
-  if ((rc = upload<long long>(ctx, ctx->d_in_prefix, nullptr, ctx->I))) return rc;
-  if (ctx->h_in_prefix) cudaFreeHost(ctx->h_in_prefix);
-  ctx->h_in_prefix = nullptr;
-  CK(cudaMallocHost(&ctx->h_in_prefix, sizeof(long long) * std::max<int32_t>(ctx->I, 1)));
-  if (ctx->h_bounds) cudaFreeHost(ctx->h_bounds);
-  ctx->h_bounds = nullptr;
-  CK(cudaMallocHost(&ctx->h_bounds, 2 * sizeof(long long) * std::max<int32_t>(ctx->I, 1)));
-  if ((rc = upload<long long>(ctx, ctx->d_bounds, nullptr, 2 * (size_t)ctx->I))) return rc;
-  ctx->have_netlist = true;
-  return GATSPI_OK;
+  return guarded(ctx, [&]() -> int {
+    if (!ctx) return GATSPI_EINVAL;
+    ctx->generation++;
+    gatspi_host::Prepared r;
+    const std::string why = gatspi_host::prepare_netlist(num_inputs, num_gates, fanin_ptr, fanin_net, lut, &r);
+    if (!why.empty()) return fail(ctx, GATSPI_EINVAL, why);
+    CK(cudaSetDevice(ctx->device));
+    ctx->have_netlist = ctx->have_delays = ctx->have_stim = ctx->have_result = false;
+    ctx->tuned_nt = ctx->tuned_ipt = 0;
+    free_netlist(ctx);
+    ctx->I = r.I; ctx->G = r.G; ctx->N = r.N; ctx->P = r.P; ctx->D = r.D;
+    ctx->gate_ext = std::move(r.gate_ext);
+    ctx->net_int = std::move(r.net_int);
+    ctx->pin_ext = std::move(r.pin_ext);
+    ctx->fanin_ptr = std::move(r.fanin_ptr);
+    ctx->fanin_net = std::move(r.fanin_net);
+    ctx->net_level = std::move(r.net_level);
+    ctx->lut = std::move(r.lut);
+    ctx->lvl_gate_begin = std::move(r.lvl_gate_begin);
+    ctx->fanout = std::move(r.fanout);
+    int rc;
+    if (!r.gate_desc.empty()) {
+      if ((rc = upload(ctx, ctx->d_gate_desc, r.gate_desc.data(), r.gate_desc.size()))) return rc;
+    } else {
+      dfree(ctx->d_gate_desc);
+    }
+    if ((rc = upload(ctx, ctx->d_fanin_ptr, ctx->fanin_ptr.data(), ctx->fanin_ptr.size()))) return rc;
+    if ((rc = upload(ctx, ctx->d_fanin_net, ctx->fanin_net.data(), ctx->fanin_net.size()))) return rc;
+    if ((rc = upload(ctx, ctx->d_net_level, ctx->net_level.data(), ctx->net_level.size()))) return rc;
+    if ((rc = upload(ctx, ctx->d_lut, ctx->lut.data(), ctx->lut.size()))) return rc;
+    if ((rc = upload<unsigned long long>(ctx, ctx->d_t1, nullptr, ctx->N))) return rc;
+    if ((rc = upload<unsigned long long>(ctx, ctx->d_tc, nullptr, ctx->N))) return rc;
+    if ((rc = upload<unsigned long long>(ctx, ctx->d_digest, nullptr, ctx->N))) return rc;
+    if ((rc = upload<long long>(ctx, ctx->d_in_prefix, nullptr, ctx->I))) return rc;
+    if (ctx->h_in_prefix) cudaFreeHost(ctx->h_in_prefix);
+    ctx->h_in_prefix = nullptr;
+    CK(cudaMallocHost(&ctx->h_in_prefix, sizeof(long long) * std::max<int32_t>(ctx->I, 1)));
+    if (ctx->h_bounds) cudaFreeHost(ctx->h_bounds);
+    ctx->h_bounds = nullptr;
+    CK(cudaMallocHost(&ctx->h_bounds, 2 * sizeof(long long) * std::max<int32_t>(ctx->I, 1)));
+    if ((rc = upload<long long>(ctx, ctx->d_bounds, nullptr, 2 * (size_t)ctx->I))) return rc;
+    ctx->have_netlist = true;
+    return GATSPI_OK;
+  });
 }
 
 int gatspi_load_delays(gatspi_ctx* ctx, const int32_t* gate_delay, const int32_t* wire_delay) {
-  if (!ctx) return GATSPI_EINVAL;
-  ctx->generation++;
-  if (!ctx->have_netlist) return fail(ctx, GATSPI_ESTATE, "load a netlist before its delays");
-  gatspi_host::Prepared view;  // only the fields prepare_delays reads
-  view.G = ctx->G; view.P = ctx->P;
-  view.fanin_ptr = ctx->fanin_ptr;
-  view.pin_ext = ctx->pin_ext;
-  std::vector<int32_t> gd, wd;
-  int32_t mg = 0, mw = 0;
-  const std::string why = gatspi_host::prepare_delays(view, gate_delay, wire_delay, &gd, &wd, &mg, &mw);
-  if (!why.empty()) return fail(ctx, GATSPI_EINVAL, why);
-  CK(cudaSetDevice(ctx->device));
-  int rc;
-  if ((rc = upload(ctx, ctx->d_gate_delay, gd.data(), gd.size()))) return rc;
-  if ((rc = upload(ctx, ctx->d_wire_delay, wd.data(), wd.size()))) return rc;
-  ctx->max_gate_delay = mg;
-  ctx->max_wire_delay = mw;
-  dfree(ctx->d_gate_delta);
-  ctx->max_edit = 0;
-  ctx->delta.clear();
-  ctx->have_delays = true;
-  ctx->have_result = false;
-  return GATSPI_OK;
+  return guarded(ctx, [&]() -> int {
+    if (!ctx) return GATSPI_EINVAL;
+    ctx->generation++;
+    if (!ctx->have_netlist) return fail(ctx, GATSPI_ESTATE, "load a netlist before its delays");
+    gatspi_host::Prepared view;  // only the fields prepare_delays reads
+    view.G = ctx->G; view.P = ctx->P;
+    view.fanin_ptr = ctx->fanin_ptr;
+    view.pin_ext = ctx->pin_ext;
+    std::vector<int32_t> gd, wd;
+    int32_t mg = 0, mw = 0;
+    const std::string why = gatspi_host::prepare_delays(view, gate_delay, wire_delay, &gd, &wd, &mg, &mw);
+    if (!why.empty()) return fail(ctx, GATSPI_EINVAL, why);
+    CK(cudaSetDevice(ctx->device));
+    int rc;
+    if ((rc = upload(ctx, ctx->d_gate_delay, gd.data(), gd.size()))) return rc;
+    if ((rc = upload(ctx, ctx->d_wire_delay, wd.data(), wd.size()))) return rc;
+    ctx->max_gate_delay = mg;
+    ctx->max_wire_delay = mw;
+    dfree(ctx->d_gate_delta);
+    ctx->max_edit = 0;
+    ctx->delta.clear();
+    ctx->have_delays = true;
+    ctx->have_result = false;
+    return GATSPI_OK;
+  });
 }
 
 int gatspi_set_edit(gatspi_ctx* ctx, int32_t n_edits, const int32_t* edit_gate, const int32_t* edit_delta) {
-  if (!ctx) return GATSPI_EINVAL;
-  ctx->generation++;
-  if (!ctx->have_delays) return fail(ctx, GATSPI_ESTATE, "load delays before an edit");
-  std::vector<int32_t> delta;
-  int rc = edit_vector(ctx, n_edits, edit_gate, edit_delta, &delta);
-  if (rc) return rc;
-  ctx->have_result = false;
-  return apply_edit(ctx, std::move(delta));
+  return guarded(ctx, [&]() -> int {
+    if (!ctx) return GATSPI_EINVAL;
+    ctx->generation++;
+    if (!ctx->have_delays) return fail(ctx, GATSPI_ESTATE, "load delays before an edit");
+    std::vector<int32_t> delta;
+    int rc = edit_vector(ctx, n_edits, edit_gate, edit_delta, &delta);
+    if (rc) return rc;
+    ctx->have_result = false;
+    return apply_edit(ctx, std::move(delta));
+  });
 }
 
 int gatspi_set_stimulus(gatspi_ctx* ctx, int32_t num_cycles, int32_t cycle_ps, const uint8_t* init,
                         const int64_t* edge_ptr, const int32_t* edge_time) {
-  if (!ctx) return GATSPI_EINVAL;
-  nvtx_range range("gatspi_set_stimulus");
-  ctx->generation++;
-  if (!ctx->have_netlist) return fail(ctx, GATSPI_ESTATE, "load a netlist before the stimulus");
-  // the arrays' shape on the host; their contents are checked on the device
-  if (num_cycles < 1 || cycle_ps < 1) return fail(ctx, GATSPI_EINVAL, "num_cycles and cycle_ps must be >= 1");
-  if (!init || !edge_ptr) return fail(ctx, GATSPI_EINVAL, "null stimulus array");
-  const int64_t n = (int64_t)ctx->I * num_cycles;
-  if (edge_ptr[0] != 0) return fail(ctx, GATSPI_EINVAL, "edge_ptr[0] must be 0");
-  const int64_t total = edge_ptr[n];
-  if (total < 0) return fail(ctx, GATSPI_EINVAL, "edge_ptr must be non-decreasing");
-  if (total > 0 && !edge_time) return fail(ctx, GATSPI_EINVAL, "null edge_time");
-  for (int32_t i = 0; i < ctx->I; ++i)
-    if (init[i] > 1) return fail(ctx, GATSPI_EINVAL, "initial values must be 0 or 1");
-  CK(cudaSetDevice(ctx->device));
-  ctx->have_stim = ctx->have_result = false;
-  int rc;
-  // device buffers are kept and reused while they are large enough
-  if ((rc = upload_reuse(ctx, ctx->d_edge_ptr, ctx->cap_edge_ptr, edge_ptr, (size_t)n + 1))) return rc;
-  if ((rc = upload_reuse(ctx, ctx->d_edge_time, ctx->cap_edge_time, edge_time, (size_t)total))) return rc;
-  if ((rc = upload_reuse(ctx, ctx->d_init_in, ctx->cap_init_in, init, (size_t)ctx->I))) return rc;
-  if (!ctx->d_first_bad) CK(cudaMalloc(&ctx->d_first_bad, sizeof(unsigned long long)));
-  const unsigned long long none = ~0ull;
-  CK(cudaMemsetAsync(ctx->d_status, 0, sizeof(int32_t), ctx->stream));
-  CK(cudaMemcpyAsync(ctx->d_first_bad, &none, sizeof(none), cudaMemcpyHostToDevice, ctx->stream));
-  stimulus_check_kernel<<<(unsigned)((n + 255) / 256), 256, 0, ctx->stream>>>(
-      ctx->d_edge_ptr, ctx->d_edge_time, n, total, cycle_ps, ctx->d_status, ctx->d_first_bad);
-  CK(cudaGetLastError());
-  int32_t status = 0;
-  unsigned long long bad = 0;
-  CK(cudaMemcpyAsync(&status, ctx->d_status, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream));
-  CK(cudaMemcpyAsync(&bad, ctx->d_first_bad, sizeof(bad), cudaMemcpyDeviceToHost, ctx->stream));
-  CK(cudaStreamSynchronize(ctx->stream));
-  if (status) {
-    const std::string where = " (input " + std::to_string(bad / (unsigned long long)num_cycles) + " cycle " +
-                              std::to_string(bad % (unsigned long long)num_cycles) + ")";
-    if (status & kStimOrder) return fail(ctx, GATSPI_EINVAL, "edge_ptr must be non-decreasing" + where);
-    if (status & kStimRange) return fail(ctx, GATSPI_EINVAL, "edge time outside [0, cycle_ps)" + where);
-    return fail(ctx, GATSPI_EINVAL, "edge times must increase strictly within a cycle" + where);
-  }
-  ctx->C = num_cycles;
-  ctx->L = cycle_ps;
-  ctx->init_in.assign(init, init + ctx->I);
-  ctx->have_stim = true;
-  return GATSPI_OK;
+  return guarded(ctx, [&]() -> int {
+    if (!ctx) return GATSPI_EINVAL;
+    nvtx_range range("gatspi_set_stimulus");
+    ctx->generation++;
+    if (!ctx->have_netlist) return fail(ctx, GATSPI_ESTATE, "load a netlist before the stimulus");
+    // the arrays' shape on the host; their contents are checked on the device
+    if (num_cycles < 1 || cycle_ps < 1) return fail(ctx, GATSPI_EINVAL, "num_cycles and cycle_ps must be >= 1");
+    if (!init || !edge_ptr) return fail(ctx, GATSPI_EINVAL, "null stimulus array");
+    const int64_t n = (int64_t)ctx->I * num_cycles;
+    if (edge_ptr[0] != 0) return fail(ctx, GATSPI_EINVAL, "edge_ptr[0] must be 0");
+    const int64_t total = edge_ptr[n];
+    if (total < 0) return fail(ctx, GATSPI_EINVAL, "edge_ptr must be non-decreasing");
+    if (total > 0 && !edge_time) return fail(ctx, GATSPI_EINVAL, "null edge_time");
+    for (int32_t i = 0; i < ctx->I; ++i)
+      if (init[i] > 1) return fail(ctx, GATSPI_EINVAL, "initial values must be 0 or 1");
+    CK(cudaSetDevice(ctx->device));
+    ctx->have_stim = ctx->have_result = false;
+    int rc;
+    // device buffers are kept and reused while they are large enough
+    if ((rc = upload_reuse(ctx, ctx->d_edge_ptr, ctx->cap_edge_ptr, edge_ptr, (size_t)n + 1))) return rc;
+    if ((rc = upload_reuse(ctx, ctx->d_edge_time, ctx->cap_edge_time, edge_time, (size_t)total))) return rc;
+    if ((rc = upload_reuse(ctx, ctx->d_init_in, ctx->cap_init_in, init, (size_t)ctx->I))) return rc;
+    if (!ctx->d_first_bad) CK(cudaMalloc(&ctx->d_first_bad, sizeof(unsigned long long)));
+    const unsigned long long none = ~0ull;
+    CK(cudaMemsetAsync(ctx->d_status, 0, sizeof(int32_t), ctx->stream));
+    CK(cudaMemcpyAsync(ctx->d_first_bad, &none, sizeof(none), cudaMemcpyHostToDevice, ctx->stream));
+    stimulus_check_kernel<<<(unsigned)((n + 255) / 256), 256, 0, ctx->stream>>>(
+        ctx->d_edge_ptr, ctx->d_edge_time, n, total, cycle_ps, ctx->d_status, ctx->d_first_bad);
+    CK(cudaGetLastError());
+    int32_t status = 0;
+    unsigned long long bad = 0;
+    CK(cudaMemcpyAsync(&status, ctx->d_status, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(&bad, ctx->d_first_bad, sizeof(bad), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (status) {
+      const std::string where = " (input " + std::to_string(bad / (unsigned long long)num_cycles) + " cycle " +
+                                std::to_string(bad % (unsigned long long)num_cycles) + ")";
+      if (status & kStimOrder) return fail(ctx, GATSPI_EINVAL, "edge_ptr must be non-decreasing" + where);
+      if (status & kStimRange) return fail(ctx, GATSPI_EINVAL, "edge time outside [0, cycle_ps)" + where);
+      return fail(ctx, GATSPI_EINVAL, "edge times must increase strictly within a cycle" + where);
+    }
+    ctx->C = num_cycles;
+    ctx->L = cycle_ps;
+    ctx->init_in.assign(init, init + ctx->I);
+    ctx->have_stim = true;
+    return GATSPI_OK;
+  });
 }
 
 int gatspi_set_stimulus_events(gatspi_ctx* ctx, int32_t num_cycles, int32_t cycle_ps, const uint8_t* init,
                                int64_t num_events, const int32_t* ev_input, const int64_t* ev_time) {
-  if (!ctx) return GATSPI_EINVAL;
-  nvtx_range range("gatspi_set_stimulus_events");
-  ctx->generation++;
-  if (!ctx->have_netlist) return fail(ctx, GATSPI_ESTATE, "load a netlist before the stimulus");
-  if (num_cycles < 1 || cycle_ps < 1) return fail(ctx, GATSPI_EINVAL, "num_cycles and cycle_ps must be >= 1");
-  if (!init || num_events < 0 || (num_events > 0 && (!ev_input || !ev_time)))
-    return fail(ctx, GATSPI_EINVAL, "null or negative stimulus arguments");
-  for (int32_t i = 0; i < ctx->I; ++i)
-    if (init[i] > 1) return fail(ctx, GATSPI_EINVAL, "initial values must be 0 or 1");
-  CK(cudaSetDevice(ctx->device));
-  ctx->have_stim = ctx->have_result = false;
-  const int64_t nb = (int64_t)ctx->I * num_cycles;  // (input, cycle) buckets
-  const int64_t n = num_events;
-  int32_t* d_in = nullptr;
-  int64_t* d_t = nullptr;
-  int32_t* d_cnt = nullptr;
-  long long* d_blk = nullptr;
-  const int64_t nblk = (nb + kScanItems - 1) / kScanItems;
-  auto cleanup = [&]() { dfree(d_in); dfree(d_t); dfree(d_cnt); dfree(d_blk); };
-  if (cudaMalloc(&d_in, sizeof(int32_t) * std::max<int64_t>(n, 1)) != cudaSuccess ||
-      cudaMalloc(&d_t, sizeof(int64_t) * std::max<int64_t>(n, 1)) != cudaSuccess ||
-      cudaMalloc(&d_cnt, sizeof(int32_t) * nb) != cudaSuccess ||
-      cudaMalloc(&d_blk, sizeof(long long) * std::max<int64_t>(nblk, 1)) != cudaSuccess) {
-    cudaGetLastError();
+  return guarded(ctx, [&]() -> int {
+    if (!ctx) return GATSPI_EINVAL;
+    nvtx_range range("gatspi_set_stimulus_events");
+    ctx->generation++;
+    if (!ctx->have_netlist) return fail(ctx, GATSPI_ESTATE, "load a netlist before the stimulus");
+    if (num_cycles < 1 || cycle_ps < 1) return fail(ctx, GATSPI_EINVAL, "num_cycles and cycle_ps must be >= 1");
+    if (!init || num_events < 0 || (num_events > 0 && (!ev_input || !ev_time)))
+      return fail(ctx, GATSPI_EINVAL, "null or negative stimulus arguments");
+    for (int32_t i = 0; i < ctx->I; ++i)
+      if (init[i] > 1) return fail(ctx, GATSPI_EINVAL, "initial values must be 0 or 1");
+    CK(cudaSetDevice(ctx->device));
+    ctx->have_stim = ctx->have_result = false;
+    const int64_t nb = (int64_t)ctx->I * num_cycles;  // (input, cycle) buckets
+    const int64_t n = num_events;
+    int32_t* d_in = nullptr;
+    int64_t* d_t = nullptr;
+    int32_t* d_cnt = nullptr;
+    long long* d_blk = nullptr;
+    const int64_t nblk = (nb + kScanItems - 1) / kScanItems;
+    auto cleanup = [&]() { dfree(d_in); dfree(d_t); dfree(d_cnt); dfree(d_blk); };
+    if (cudaMalloc(&d_in, sizeof(int32_t) * std::max<int64_t>(n, 1)) != cudaSuccess ||
+        cudaMalloc(&d_t, sizeof(int64_t) * std::max<int64_t>(n, 1)) != cudaSuccess ||
+        cudaMalloc(&d_cnt, sizeof(int32_t) * nb) != cudaSuccess ||
+        cudaMalloc(&d_blk, sizeof(long long) * std::max<int64_t>(nblk, 1)) != cudaSuccess) {
+      cudaGetLastError();
+      cleanup();
+      return fail(ctx, GATSPI_ENOMEM, "stimulus ingest buffers");
+    }
+    int rc = upload_reuse(ctx, ctx->d_edge_ptr, ctx->cap_edge_ptr, (const int64_t*)nullptr, (size_t)nb + 1);
+    if (!rc) rc = upload_reuse(ctx, ctx->d_edge_time, ctx->cap_edge_time, (const int32_t*)nullptr, (size_t)n);
+    if (!rc) rc = upload_reuse(ctx, ctx->d_init_in, ctx->cap_init_in, init, (size_t)ctx->I);
+    if (rc) {
+      cleanup();
+      return rc;
+    }
+    IngestParams q{};
+    q.ev_input = d_in; q.ev_time = d_t; q.n = n; q.I = ctx->I; q.C = num_cycles; q.L = cycle_ps;
+    q.counts = d_cnt; q.edge_ptr = ctx->d_edge_ptr; q.edge_time = ctx->d_edge_time; q.status = ctx->d_status;
+    int32_t status = 0;
+    cudaStream_t st = ctx->stream;
+    const unsigned eb = (unsigned)std::max<int64_t>(1, (n + 255) / 256);
+    const unsigned bb = (unsigned)((nb + 255) / 256);
+    cudaError_t e = cudaSuccess;
+    do {
+      if (n && ((e = cudaMemcpyAsync(d_in, ev_input, sizeof(int32_t) * n, cudaMemcpyHostToDevice, st)) ||
+                (e = cudaMemcpyAsync(d_t, ev_time, sizeof(int64_t) * n, cudaMemcpyHostToDevice, st))))
+        break;
+      if ((e = cudaMemsetAsync(ctx->d_status, 0, sizeof(int32_t), st)) ||
+          (e = cudaMemsetAsync(d_cnt, 0, sizeof(int32_t) * nb, st)))
+        break;
+      if (n) ingest_bucket_kernel<<<eb, 256, 0, st>>>(q);
+      scan_totals_kernel<<<(unsigned)nblk, kScanThreads, 0, st>>>(d_cnt, nb, d_blk);
+      scan_blocks_kernel<<<1, kScanThreads, 0, st>>>(d_blk, nblk);
+      scan_apply_kernel<<<(unsigned)nblk, kScanThreads, 0, st>>>(d_cnt, nb, d_blk, ctx->d_edge_ptr);
+      if ((e = cudaMemsetAsync(d_cnt, 0, sizeof(int32_t) * nb, st))) break;
+      if (n) ingest_scatter_kernel<<<eb, 256, 0, st>>>(q);
+      ingest_order_kernel<<<bb, 256, 0, st>>>(q);
+      if ((e = cudaGetLastError())) break;
+      if ((e = cudaMemcpyAsync(&status, ctx->d_status, sizeof(int32_t), cudaMemcpyDeviceToHost, st)) ||
+          (e = cudaStreamSynchronize(st)))
+        break;
+    } while (0);
     cleanup();
-    return fail(ctx, GATSPI_ENOMEM, "stimulus ingest buffers");
-  }
-  int rc = upload_reuse(ctx, ctx->d_edge_ptr, ctx->cap_edge_ptr, (const int64_t*)nullptr, (size_t)nb + 1);
-  if (!rc) rc = upload_reuse(ctx, ctx->d_edge_time, ctx->cap_edge_time, (const int32_t*)nullptr, (size_t)n);
-  if (!rc) rc = upload_reuse(ctx, ctx->d_init_in, ctx->cap_init_in, init, (size_t)ctx->I);
-  if (rc) {
-    cleanup();
-    return rc;
-  }
-  IngestParams q{};
-  q.ev_input = d_in; q.ev_time = d_t; q.n = n; q.I = ctx->I; q.C = num_cycles; q.L = cycle_ps;
-  q.counts = d_cnt; q.edge_ptr = ctx->d_edge_ptr; q.edge_time = ctx->d_edge_time; q.status = ctx->d_status;
-  int32_t status = 0;
-  cudaStream_t st = ctx->stream;
-  const unsigned eb = (unsigned)std::max<int64_t>(1, (n + 255) / 256);
-  const unsigned bb = (unsigned)((nb + 255) / 256);
-  cudaError_t e = cudaSuccess;
-  do {
-    if (n && ((e = cudaMemcpyAsync(d_in, ev_input, sizeof(int32_t) * n, cudaMemcpyHostToDevice, st)) ||
-              (e = cudaMemcpyAsync(d_t, ev_time, sizeof(int64_t) * n, cudaMemcpyHostToDevice, st))))
-      break;
-    if ((e = cudaMemsetAsync(ctx->d_status, 0, sizeof(int32_t), st)) ||
-        (e = cudaMemsetAsync(d_cnt, 0, sizeof(int32_t) * nb, st)))
-      break;
-    if (n) ingest_bucket_kernel<<<eb, 256, 0, st>>>(q);
-    scan_totals_kernel<<<(unsigned)nblk, kScanThreads, 0, st>>>(d_cnt, nb, d_blk);
-    scan_blocks_kernel<<<1, kScanThreads, 0, st>>>(d_blk, nblk);
-    scan_apply_kernel<<<(unsigned)nblk, kScanThreads, 0, st>>>(d_cnt, nb, d_blk, ctx->d_edge_ptr);
-    if ((e = cudaMemsetAsync(d_cnt, 0, sizeof(int32_t) * nb, st))) break;
-    if (n) ingest_scatter_kernel<<<eb, 256, 0, st>>>(q);
-    ingest_order_kernel<<<bb, 256, 0, st>>>(q);
-    if ((e = cudaGetLastError())) break;
-    if ((e = cudaMemcpyAsync(&status, ctx->d_status, sizeof(int32_t), cudaMemcpyDeviceToHost, st)) ||
-        (e = cudaStreamSynchronize(st)))
-      break;
-  } while (0);
-  cleanup();
-  if (e != cudaSuccess) return fail(ctx, GATSPI_ECUDA, std::string("stimulus ingest: ") + cudaGetErrorString(e));
-  if (status & kIngBadInput) return fail(ctx, GATSPI_EINVAL, "an event names an input outside [0, I)");
-  if (status & kIngBadTime) return fail(ctx, GATSPI_EINVAL, "an event time lies outside [0, num_cycles * cycle_ps)");
-  if (status & kIngTwice) return fail(ctx, GATSPI_EINVAL, "an input toggles twice at the same time");
-  ctx->C = num_cycles;
-  ctx->L = cycle_ps;
-  ctx->init_in.assign(init, init + ctx->I);
-  ctx->have_stim = true;
-  return GATSPI_OK;
+    if (e != cudaSuccess) return fail(ctx, GATSPI_ECUDA, std::string("stimulus ingest: ") + cudaGetErrorString(e));
+    if (status & kIngBadInput) return fail(ctx, GATSPI_EINVAL, "an event names an input outside [0, I)");
+    if (status & kIngBadTime) return fail(ctx, GATSPI_EINVAL, "an event time lies outside [0, num_cycles * cycle_ps)");
+    if (status & kIngTwice) return fail(ctx, GATSPI_EINVAL, "an input toggles twice at the same time");
+    ctx->C = num_cycles;
+    ctx->L = cycle_ps;
+    ctx->init_in.assign(init, init + ctx->I);
+    ctx->have_stim = true;
+    return GATSPI_OK;
+  });
 }
 
 }  // extern "C"
@@ -919,324 +951,336 @@ int autotune(gatspi_ctx* ctx, const gatspi_opts& base) {
 extern "C" {
 
 int gatspi_simulate(gatspi_ctx* ctx, const gatspi_opts* opts) {
-  if (!ctx) return GATSPI_EINVAL;
-  nvtx_range range("gatspi_simulate");
-  if (!ctx->have_netlist || !ctx->have_delays || !ctx->have_stim)
-    return fail(ctx, GATSPI_ESTATE, "load a netlist, its delays and a stimulus first");
-  gatspi_opts o{};
-  if (opts) o = *opts;
-  const bool pp = o.pulse_limits == 1 && (o.gate_pulse_percent != 100 || o.wire_pulse_percent != 100);
-  if (o.tile_items == 0 && o.items_per_thread == 0 && !pp) {
-    if (!ctx->tuned_nt) {
-      const int rc = autotune(ctx, o);
-      if (rc) return rc;
+  return guarded(ctx, [&]() -> int {
+    if (!ctx) return GATSPI_EINVAL;
+    nvtx_range range("gatspi_simulate");
+    if (!ctx->have_netlist || !ctx->have_delays || !ctx->have_stim)
+      return fail(ctx, GATSPI_ESTATE, "load a netlist, its delays and a stimulus first");
+    gatspi_opts o{};
+    if (opts) o = *opts;
+    const bool pp = o.pulse_limits == 1 && (o.gate_pulse_percent != 100 || o.wire_pulse_percent != 100);
+    if (o.tile_items == 0 && o.items_per_thread == 0 && !pp) {
+      if (!ctx->tuned_nt) {
+        const int rc = autotune(ctx, o);
+        if (rc) return rc;
+      }
+      o.tile_items = ctx->tuned_nt;
+      o.items_per_thread = ctx->tuned_ipt;
     }
-    o.tile_items = ctx->tuned_nt;
-    o.items_per_thread = ctx->tuned_ipt;
-  }
-  const int rc = simulate_impl(ctx, &o);
-  if (rc == GATSPI_OK) {
-    ctx->have_last_opts = true;
-    ctx->last_opts = o;
-    ctx->last_opts.tile_items = ctx->stats.tile_threads;
-    ctx->last_opts.items_per_thread = ctx->stats.items_per_thread;
-  }
-  return rc;
+    const int rc = simulate_impl(ctx, &o);
+    if (rc == GATSPI_OK) {
+      ctx->have_last_opts = true;
+      ctx->last_opts = o;
+      ctx->last_opts.tile_items = ctx->stats.tile_threads;
+      ctx->last_opts.items_per_thread = ctx->stats.items_per_thread;
+    }
+    return rc;
+  });
 }
 
 int gatspi_resimulate_edit(gatspi_ctx* ctx, int32_t n_edits, const int32_t* edit_gate,
                            const int32_t* edit_delta, gatspi_resim_info* info) {
-  if (!ctx) return GATSPI_EINVAL;
-  nvtx_range range("gatspi_resimulate_edit");
-  if (!ctx->have_last_opts) return fail(ctx, GATSPI_ESTATE, "simulate once before re-simulating an edit");
-  if (!ctx->have_netlist || !ctx->have_delays || !ctx->have_stim)
-    return fail(ctx, GATSPI_ESTATE, "load a netlist, its delays and a stimulus first");
-  std::vector<int32_t> nd;
-  int rc = edit_vector(ctx, n_edits, edit_gate, edit_delta, &nd);
-  if (rc) return rc;
-  gatspi_resim_info r{};
-  const auto t_start = std::chrono::steady_clock::now();
-  const bool resident = ctx->have_result && ctx->result_single && ctx->result_gen == ctx->generation;
-  const bool current = ctx->have_result;  // the results match the loaded inputs and edit
-  // gates whose delays change: the cone's roots
-  std::vector<uint8_t> in_cone(ctx->G, 0);
-  int32_t roots = 0;
-  for (int32_t g = 0; g < ctx->G; ++g) {
-    const int32_t a = ctx->delta.empty() ? 0 : ctx->delta[g];
-    const int32_t b = nd.empty() ? 0 : nd[g];
-    if (a != b) {
-      in_cone[g] = 1;
-      ++roots;
+  return guarded(ctx, [&]() -> int {
+    if (!ctx) return GATSPI_EINVAL;
+    nvtx_range range("gatspi_resimulate_edit");
+    if (!ctx->have_last_opts) return fail(ctx, GATSPI_ESTATE, "simulate once before re-simulating an edit");
+    if (!ctx->have_netlist || !ctx->have_delays || !ctx->have_stim)
+      return fail(ctx, GATSPI_ESTATE, "load a netlist, its delays and a stimulus first");
+    std::vector<int32_t> nd;
+    int rc = edit_vector(ctx, n_edits, edit_gate, edit_delta, &nd);
+    if (rc) return rc;
+    gatspi_resim_info r{};
+    const auto t_start = std::chrono::steady_clock::now();
+    const bool resident = ctx->have_result && ctx->result_single && ctx->result_gen == ctx->generation;
+    const bool current = ctx->have_result;  // the results match the loaded inputs and edit
+    // gates whose delays change: the cone's roots
+    std::vector<uint8_t> in_cone(ctx->G, 0);
+    int32_t roots = 0;
+    for (int32_t g = 0; g < ctx->G; ++g) {
+      const int32_t a = ctx->delta.empty() ? 0 : ctx->delta[g];
+      const int32_t b = nd.empty() ? 0 : nd[g];
+      if (a != b) {
+        in_cone[g] = 1;
+        ++roots;
+      }
     }
-  }
-  ctx->generation++;
-  if ((rc = apply_edit(ctx, std::move(nd)))) {
-    ctx->have_result = false;
-    return rc;
-  }
-  const gatspi_opts o = ctx->last_opts;
-  auto full = [&]() {
-    r.mode = 2;
-    const int e = simulate_impl(ctx, &o);
-    r.cone_gates = ctx->G;
-    r.first_level = 1;
-    r.levels = ctx->D;
-    r.items = (int64_t)ctx->G * ctx->n_windows;
-    if (info) *info = r;
-    return e;
-  };
-  if (roots == 0 && current) {  // nothing changes: the results stand
-    if (resident) ctx->result_gen = ctx->generation;
+    ctx->generation++;
+    if ((rc = apply_edit(ctx, std::move(nd)))) {
+      ctx->have_result = false;
+      return rc;
+    }
+    const gatspi_opts o = ctx->last_opts;
+    auto full = [&]() {
+      r.mode = 2;
+      const int e = simulate_impl(ctx, &o);
+      r.cone_gates = ctx->G;
+      r.first_level = 1;
+      r.levels = ctx->D;
+      r.items = (int64_t)ctx->G * ctx->n_windows;
+      if (info) *info = r;
+      return e;
+    };
+    if (roots == 0 && current) {  // nothing changes: the results stand
+      if (resident) ctx->result_gen = ctx->generation;
+      if (info) *info = r;
+      return GATSPI_OK;
+    }
+    if (!resident) return full();
+    // the fanout cone of the changed gates, level by level (gates are sorted
+    // by level, so one pass in gate order reaches every cone gate after its
+    // fanins)
+    if (ctx->fo_ptr.empty()) {
+      ctx->fo_ptr.assign((size_t)ctx->N + 1, 0);
+      for (int32_t p = 0; p < ctx->P; ++p) ctx->fo_ptr[ctx->fanin_net[p] + 1]++;
+      for (int32_t n = 0; n < ctx->N; ++n) ctx->fo_ptr[n + 1] += ctx->fo_ptr[n];
+      ctx->fo_gate.assign((size_t)ctx->P, 0);
+      std::vector<int32_t> fill(ctx->fo_ptr.begin(), ctx->fo_ptr.end() - 1);
+      for (int32_t g = 0; g < ctx->G; ++g)
+        for (int32_t p = ctx->fanin_ptr[g]; p < ctx->fanin_ptr[g + 1]; ++p) ctx->fo_gate[fill[ctx->fanin_net[p]]++] = g;
+    }
+    std::vector<int32_t> list;
+    std::vector<int32_t> lvl_off((size_t)ctx->D + 2, 0);  // cone gates of level l: list[lvl_off[l] .. lvl_off[l+1])
+    for (int32_t l = 1; l <= ctx->D; ++l) {
+      lvl_off[l] = (int32_t)list.size();
+      for (int32_t g = ctx->lvl_gate_begin[l]; g < ctx->lvl_gate_begin[l + 1]; ++g) {
+        if (!in_cone[g]) continue;
+        list.push_back(g);
+        const int32_t net = ctx->I + g;
+        for (int32_t k = ctx->fo_ptr[net]; k < ctx->fo_ptr[net + 1]; ++k) in_cone[ctx->fo_gate[k]] = 1;
+      }
+    }
+    lvl_off[ctx->D + 1] = (int32_t)list.size();
+    const int32_t nw = ctx->batch_nw, T = ctx->batch_T;
+    // room for the cone's new runs: at least twice the edges the cone's nets
+    // hold now, else the whole batch is simulated again (which also compacts)
+    std::vector<unsigned long long> tc(ctx->N);
+    CK(cudaMemcpy(tc.data(), ctx->d_tc, sizeof(unsigned long long) * ctx->N, cudaMemcpyDeviceToHost));
+    int64_t old_edges = 0;
+    for (int32_t g : list) old_edges += (int64_t)tc[(size_t)ctx->I + g];
+    if (ctx->append_ptr + 2 * old_edges + (1 << 16) > ctx->times_cap) return full();
+    if (!ctx->d_cone) {
+      CK(cudaMalloc(&ctx->d_cone, sizeof(int32_t) * std::max<int32_t>(ctx->G, 1)));
+    }
+    if (!ctx->d_append) CK(cudaMalloc(&ctx->d_append, 2 * sizeof(long long)));
+    CK(cudaMemcpy(ctx->d_cone, list.data(), sizeof(int32_t) * list.size(), cudaMemcpyHostToDevice));
+    const long long ap = ctx->append_ptr;
+    CK(cudaMemcpy(ctx->d_append, &ap, sizeof(long long), cudaMemcpyHostToDevice));
+    const int32_t pulse_g = o.pulse_limits ? o.gate_pulse_percent : 100;
+    const int32_t pulse_w = o.pulse_limits ? o.wire_pulse_percent : 100;
+    const bool pp = pulse_g != 100 || pulse_w != 100;
+    const int nt = o.tile_items, ipt = o.items_per_thread;
+    if (ctx->ev.size() < 2) {
+      for (auto e : ctx->ev) cudaEventDestroy(e);
+      ctx->ev.assign(2, nullptr);
+      for (auto& e : ctx->ev) CK(cudaEventCreate(&e));
+    }
+    cudaEvent_t e0 = ctx->ev[0], e1 = ctx->ev[1];
+    CK(cudaMemsetAsync(ctx->d_status, 0, sizeof(int32_t), ctx->stream));
+    CK(cudaEventRecord(e0, ctx->stream));
+    clear_saif_kernel<<<(unsigned)((list.size() + 255) / 256), 256, 0, ctx->stream>>>(
+        (int32_t)list.size(), ctx->d_cone, ctx->I, ctx->d_t1, ctx->d_tc);
+    CK(cudaGetLastError());
+    const JobView job = job_view(ctx, nw, ctx->batch_w0, ctx->W, pulse_g, pulse_w);
+    int32_t k = 0;
+    for (int32_t l = 1; l <= ctx->D; ++l) {
+      const int32_t nc = lvl_off[l + 1] - lvl_off[l];
+      if (nc == 0) continue;
+      if (r.levels == 0) r.first_level = l;
+      CK(cudaMemsetAsync(ctx->d_counters + l, 0, sizeof(unsigned long long), ctx->stream));
+      CK(cudaMemsetAsync(ctx->d_tile_counter + l, 0, sizeof(int32_t), ctx->stream));
+      PropParams p{};
+      p.job = job;
+      p.seg.counters = ctx->d_counters + l;
+      p.seg.level = l;
+      p.seg.gate_begin = ctx->lvl_gate_begin[l];
+      p.seg.n_items = nc * nw;
+      p.seg.n_tiles = nc * T;
+      p.seg.gate_list = ctx->d_cone + lvl_off[l];
+      p.seg.append_in = ctx->d_append + (k & 1);
+      p.seg.append_out = ctx->d_append + ((k + 1) & 1);
+      p.tile_counter = ctx->d_tile_counter + l;
+      if (pp) {
+        SingleLaunchMode<kModePulse> go{&p, ctx->stream};
+        launch_variant_pp(nt, ipt, go);
+      } else {
+        SingleLaunchMode<kModeCone> go{&p, ctx->stream};
+        launch_variant_cone(ipt, go);
+      }
+      CK(cudaGetLastError());
+      ++k;
+      ++r.levels;
+      r.items += (int64_t)nc * nw;
+    }
+    CK(cudaEventRecord(e1, ctx->stream));
+    if (o.digest) {
+      CK(cudaMemsetAsync(ctx->d_digest, 0, sizeof(unsigned long long) * ctx->N, ctx->stream));
+      DigestParams q{};
+      q.rmeta = ctx->d_rmeta; q.tinfo = ctx->d_tinfo; q.rstart = ctx->d_rstart;
+      q.net_level = ctx->d_net_level; q.lvl_base = ctx->d_lvl_base; q.times = ctx->d_times;
+      q.capacity = ctx->times_cap; q.out = ctx->d_digest; q.status = ctx->d_status;
+      q.N = ctx->N; q.NW = nw; q.w0 = ctx->batch_w0;
+      q.TW = ctx->batch_TW;
+      q.T = T;
+      const long long warps = (long long)q.N * q.T;
+      digest_kernel<<<(unsigned)((warps + 7) / 8), 256, 0, ctx->stream>>>(q);
+      CK(cudaGetLastError());
+    }
+    CK(cudaMemcpyAsync(&ctx->h_ret[0], ctx->d_status, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(&ctx->h_ret[1], ctx->d_append + (k & 1), sizeof(long long), cudaMemcpyDeviceToHost,
+                       ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    const int32_t status = (int32_t)ctx->h_ret[0];
+    if (status & kStTimeout) {
+      ctx->have_result = false;
+      return fail(ctx, GATSPI_ETIMEOUT, "a device-side wait ran out");
+    }
+    // a cone that outgrew the append region (or int32 run offsets): the whole
+    // batch again, from scratch
+    if (status & (kStCapacity | kStOffset | kStCorrupt)) return full();
+    ctx->append_ptr = ctx->h_ret[1];
+    ctx->result_gen = ctx->generation;
+    r.mode = 1;
+    r.cone_gates = (int32_t)list.size();
+    // figures of this call: the cone's launches
+    gatspi_stats st = ctx->stats;
+    float ms = 0;
+    CK(cudaEventElapsedTime(&ms, e0, e1));
+    st.prop_ms = ms;
+    st.device_ms = ms;
+    st.input_ms = 0;
+    st.kernel_launches = 1 + r.levels + (o.digest ? 1 : 0);
+    st.prop_launches = r.levels;
+    st.items = r.items;
+    CK(cudaMemcpy(tc.data(), ctx->d_tc, sizeof(unsigned long long) * ctx->N, cudaMemcpyDeviceToHost));
+    int64_t edges = 0, bytes = 0;
+    for (int32_t n = 0; n < ctx->N; ++n) edges += (int64_t)tc[n];
+    for (int32_t g : list) {
+      const int32_t pins = ctx->fanin_ptr[g + 1] - ctx->fanin_ptr[g];
+      bytes += (int64_t)(pins + 1) * (2ll * nw + 8ll * T) + 4ll * (int64_t)tc[(size_t)ctx->I + g];
+      for (int32_t p = ctx->fanin_ptr[g]; p < ctx->fanin_ptr[g + 1]; ++p) bytes += 4ll * (int64_t)tc[ctx->fanin_net[p]];
+    }
+    st.edges = edges;
+    st.algo_bytes = bytes;
+    st.wall_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
+    ctx->stats = st;
     if (info) *info = r;
     return GATSPI_OK;
-  }
-  if (!resident) return full();
-  // the fanout cone of the changed gates, level by level (gates are sorted
-  // by level, so one pass in gate order reaches every cone gate after its
-  // fanins)
-  if (ctx->fo_ptr.empty()) {
-    ctx->fo_ptr.assign((size_t)ctx->N + 1, 0);
-    for (int32_t p = 0; p < ctx->P; ++p) ctx->fo_ptr[ctx->fanin_net[p] + 1]++;
-    for (int32_t n = 0; n < ctx->N; ++n) ctx->fo_ptr[n + 1] += ctx->fo_ptr[n];
-    ctx->fo_gate.assign((size_t)ctx->P, 0);
-    std::vector<int32_t> fill(ctx->fo_ptr.begin(), ctx->fo_ptr.end() - 1);
-    for (int32_t g = 0; g < ctx->G; ++g)
-      for (int32_t p = ctx->fanin_ptr[g]; p < ctx->fanin_ptr[g + 1]; ++p) ctx->fo_gate[fill[ctx->fanin_net[p]]++] = g;
-  }
-  std::vector<int32_t> list;
-  std::vector<int32_t> lvl_off((size_t)ctx->D + 2, 0);  // cone gates of level l: list[lvl_off[l] .. lvl_off[l+1])
-  for (int32_t l = 1; l <= ctx->D; ++l) {
-    lvl_off[l] = (int32_t)list.size();
-    for (int32_t g = ctx->lvl_gate_begin[l]; g < ctx->lvl_gate_begin[l + 1]; ++g) {
-      if (!in_cone[g]) continue;
-      list.push_back(g);
-      const int32_t net = ctx->I + g;
-      for (int32_t k = ctx->fo_ptr[net]; k < ctx->fo_ptr[net + 1]; ++k) in_cone[ctx->fo_gate[k]] = 1;
-    }
-  }
-  lvl_off[ctx->D + 1] = (int32_t)list.size();
-  const int32_t nw = ctx->batch_nw, T = ctx->batch_T;
-  // room for the cone's new runs: at least twice the edges the cone's nets
-  // hold now, else the whole batch is simulated again (which also compacts)
-  std::vector<unsigned long long> tc(ctx->N);
-  CK(cudaMemcpy(tc.data(), ctx->d_tc, sizeof(unsigned long long) * ctx->N, cudaMemcpyDeviceToHost));
-  int64_t old_edges = 0;
-  for (int32_t g : list) old_edges += (int64_t)tc[(size_t)ctx->I + g];
-  if (ctx->append_ptr + 2 * old_edges + (1 << 16) > ctx->times_cap) return full();
-  if (!ctx->d_cone) {
-    CK(cudaMalloc(&ctx->d_cone, sizeof(int32_t) * std::max<int32_t>(ctx->G, 1)));
-  }
-  if (!ctx->d_append) CK(cudaMalloc(&ctx->d_append, 2 * sizeof(long long)));
-  CK(cudaMemcpy(ctx->d_cone, list.data(), sizeof(int32_t) * list.size(), cudaMemcpyHostToDevice));
-  const long long ap = ctx->append_ptr;
-  CK(cudaMemcpy(ctx->d_append, &ap, sizeof(long long), cudaMemcpyHostToDevice));
-  const int32_t pulse_g = o.pulse_limits ? o.gate_pulse_percent : 100;
-  const int32_t pulse_w = o.pulse_limits ? o.wire_pulse_percent : 100;
-  const bool pp = pulse_g != 100 || pulse_w != 100;
-  const int nt = o.tile_items, ipt = o.items_per_thread;
-  if (ctx->ev.size() < 2) {
-    for (auto e : ctx->ev) cudaEventDestroy(e);
-    ctx->ev.assign(2, nullptr);
-    for (auto& e : ctx->ev) CK(cudaEventCreate(&e));
-  }
-  cudaEvent_t e0 = ctx->ev[0], e1 = ctx->ev[1];
-  CK(cudaMemsetAsync(ctx->d_status, 0, sizeof(int32_t), ctx->stream));
-  CK(cudaEventRecord(e0, ctx->stream));
-  clear_saif_kernel<<<(unsigned)((list.size() + 255) / 256), 256, 0, ctx->stream>>>(
-      (int32_t)list.size(), ctx->d_cone, ctx->I, ctx->d_t1, ctx->d_tc);
-  CK(cudaGetLastError());
-  const JobView job = job_view(ctx, nw, ctx->batch_w0, ctx->W, pulse_g, pulse_w);
-  int32_t k = 0;
-  for (int32_t l = 1; l <= ctx->D; ++l) {
-    const int32_t nc = lvl_off[l + 1] - lvl_off[l];
-    if (nc == 0) continue;
-    if (r.levels == 0) r.first_level = l;
-    CK(cudaMemsetAsync(ctx->d_counters + l, 0, sizeof(unsigned long long), ctx->stream));
-    CK(cudaMemsetAsync(ctx->d_tile_counter + l, 0, sizeof(int32_t), ctx->stream));
-    PropParams p{};
-    p.job = job;
-    p.seg.counters = ctx->d_counters + l;
-    p.seg.level = l;
-    p.seg.gate_begin = ctx->lvl_gate_begin[l];
-    p.seg.n_items = nc * nw;
-    p.seg.n_tiles = nc * T;
-    p.seg.gate_list = ctx->d_cone + lvl_off[l];
-    p.seg.append_in = ctx->d_append + (k & 1);
-    p.seg.append_out = ctx->d_append + ((k + 1) & 1);
-    p.tile_counter = ctx->d_tile_counter + l;
-    if (pp) {
-      SingleLaunchMode<kModePulse> go{&p, ctx->stream};
-      launch_variant_pp(nt, ipt, go);
-    } else {
-      SingleLaunchMode<kModeCone> go{&p, ctx->stream};
-      launch_variant_cone(ipt, go);
-    }
-    CK(cudaGetLastError());
-    ++k;
-    ++r.levels;
-    r.items += (int64_t)nc * nw;
-  }
-  CK(cudaEventRecord(e1, ctx->stream));
-  if (o.digest) {
-    CK(cudaMemsetAsync(ctx->d_digest, 0, sizeof(unsigned long long) * ctx->N, ctx->stream));
-    DigestParams q{};
-    q.rmeta = ctx->d_rmeta; q.tinfo = ctx->d_tinfo; q.rstart = ctx->d_rstart;
-    q.net_level = ctx->d_net_level; q.lvl_base = ctx->d_lvl_base; q.times = ctx->d_times;
-    q.capacity = ctx->times_cap; q.out = ctx->d_digest; q.status = ctx->d_status;
-    q.N = ctx->N; q.NW = nw; q.w0 = ctx->batch_w0;
-    q.TW = ctx->batch_TW;
-    q.T = T;
-    const long long warps = (long long)q.N * q.T;
-    digest_kernel<<<(unsigned)((warps + 7) / 8), 256, 0, ctx->stream>>>(q);
-    CK(cudaGetLastError());
-  }
-  CK(cudaMemcpyAsync(&ctx->h_ret[0], ctx->d_status, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream));
-  CK(cudaMemcpyAsync(&ctx->h_ret[1], ctx->d_append + (k & 1), sizeof(long long), cudaMemcpyDeviceToHost,
-                     ctx->stream));
-  CK(cudaStreamSynchronize(ctx->stream));
-  const int32_t status = (int32_t)ctx->h_ret[0];
-  if (status & kStTimeout) {
-    ctx->have_result = false;
-    return fail(ctx, GATSPI_ETIMEOUT, "a device-side wait ran out");
-  }
-  // a cone that outgrew the append region (or int32 run offsets): the whole
-  // batch again, from scratch
-  if (status & (kStCapacity | kStOffset | kStCorrupt)) return full();
-  ctx->append_ptr = ctx->h_ret[1];
-  ctx->result_gen = ctx->generation;
-  r.mode = 1;
-  r.cone_gates = (int32_t)list.size();
-  // figures of this call: the cone's launches
-  gatspi_stats st = ctx->stats;
-  float ms = 0;
-  CK(cudaEventElapsedTime(&ms, e0, e1));
-  st.prop_ms = ms;
-  st.device_ms = ms;
-  st.input_ms = 0;
-  st.kernel_launches = 1 + r.levels + (o.digest ? 1 : 0);
-  st.prop_launches = r.levels;
-  st.items = r.items;
-  CK(cudaMemcpy(tc.data(), ctx->d_tc, sizeof(unsigned long long) * ctx->N, cudaMemcpyDeviceToHost));
-  int64_t edges = 0, bytes = 0;
-  for (int32_t n = 0; n < ctx->N; ++n) edges += (int64_t)tc[n];
-  for (int32_t g : list) {
-    const int32_t pins = ctx->fanin_ptr[g + 1] - ctx->fanin_ptr[g];
-    bytes += (int64_t)(pins + 1) * (2ll * nw + 8ll * T) + 4ll * (int64_t)tc[(size_t)ctx->I + g];
-    for (int32_t p = ctx->fanin_ptr[g]; p < ctx->fanin_ptr[g + 1]; ++p) bytes += 4ll * (int64_t)tc[ctx->fanin_net[p]];
-  }
-  st.edges = edges;
-  st.algo_bytes = bytes;
-  st.wall_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
-  ctx->stats = st;
-  if (info) *info = r;
-  return GATSPI_OK;
+  });
 }
 
 int gatspi_saif(gatspi_ctx* ctx, int64_t* t0, int64_t* t1, int64_t* tc) {
-  if (!ctx) return GATSPI_EINVAL;
-  if (!ctx->have_result) return fail(ctx, GATSPI_ESTATE, "nothing simulated yet");
-  CK(cudaSetDevice(ctx->device));
-  std::vector<unsigned long long> a(ctx->N), b(ctx->N);
-  CK(cudaMemcpyAsync(a.data(), ctx->d_t1, sizeof(unsigned long long) * ctx->N, cudaMemcpyDeviceToHost, ctx->stream));
-  CK(cudaMemcpyAsync(b.data(), ctx->d_tc, sizeof(unsigned long long) * ctx->N, cudaMemcpyDeviceToHost, ctx->stream));
-  CK(cudaStreamSynchronize(ctx->stream));
-  for (int32_t e = 0; e < ctx->N; ++e) {
-    const int32_t n = ctx->net_int[e];
-    if (t1) t1[e] = (int64_t)a[n];
-    if (t0) t0[e] = ctx->total_time - (int64_t)a[n];
-    if (tc) tc[e] = (int64_t)b[n];
-  }
-  return GATSPI_OK;
+  return guarded(ctx, [&]() -> int {
+    if (!ctx) return GATSPI_EINVAL;
+    if (!ctx->have_result) return fail(ctx, GATSPI_ESTATE, "nothing simulated yet");
+    CK(cudaSetDevice(ctx->device));
+    std::vector<unsigned long long> a(ctx->N), b(ctx->N);
+    CK(cudaMemcpyAsync(a.data(), ctx->d_t1, sizeof(unsigned long long) * ctx->N, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(b.data(), ctx->d_tc, sizeof(unsigned long long) * ctx->N, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    for (int32_t e = 0; e < ctx->N; ++e) {
+      const int32_t n = ctx->net_int[e];
+      if (t1) t1[e] = (int64_t)a[n];
+      if (t0) t0[e] = ctx->total_time - (int64_t)a[n];
+      if (tc) tc[e] = (int64_t)b[n];
+    }
+    return GATSPI_OK;
+  });
 }
 
 int gatspi_digest(gatspi_ctx* ctx, uint64_t* out) {
-  if (!ctx || !out) return GATSPI_EINVAL;
-  if (!ctx->have_digest) return fail(ctx, GATSPI_ESTATE, "no digest: simulate with opts.digest = 1 first");
-  CK(cudaSetDevice(ctx->device));
-  std::vector<unsigned long long> d(ctx->N);
-  CK(cudaMemcpy(d.data(), ctx->d_digest, sizeof(unsigned long long) * ctx->N, cudaMemcpyDeviceToHost));
-  for (int32_t e = 0; e < ctx->N; ++e) out[e] = d[ctx->net_int[e]];
-  return GATSPI_OK;
+  return guarded(ctx, [&]() -> int {
+    if (!ctx || !out) return GATSPI_EINVAL;
+    if (!ctx->have_digest) return fail(ctx, GATSPI_ESTATE, "no digest: simulate with opts.digest = 1 first");
+    CK(cudaSetDevice(ctx->device));
+    std::vector<unsigned long long> d(ctx->N);
+    CK(cudaMemcpy(d.data(), ctx->d_digest, sizeof(unsigned long long) * ctx->N, cudaMemcpyDeviceToHost));
+    for (int32_t e = 0; e < ctx->N; ++e) out[e] = d[ctx->net_int[e]];
+    return GATSPI_OK;
+  });
 }
 
 int gatspi_read_window(gatspi_ctx* ctx, int32_t window, uint8_t* init, int64_t* ptr, int32_t* times,
                        int64_t cap, int64_t* total) {
-  if (!ctx) return GATSPI_EINVAL;
-  if (!ctx->have_result) return fail(ctx, GATSPI_ESTATE, "nothing simulated yet");
-  if (!init || !ptr) return fail(ctx, GATSPI_EINVAL, "null output array");
-  if (window < ctx->batch_w0 || window >= ctx->batch_w0 + ctx->batch_nw)
-    return fail(ctx, GATSPI_ESTATE, "window " + std::to_string(window) + " is not in the resident batch [" +
-                                        std::to_string(ctx->batch_w0) + ", " +
-                                        std::to_string(ctx->batch_w0 + ctx->batch_nw) + ")");
-  CK(cudaSetDevice(ctx->device));
-  const int32_t N = ctx->N, w = window - ctx->batch_w0;
-  int32_t* d_cnt = nullptr;
-  uint8_t* d_iv = nullptr;
-  long long* d_dst = nullptr;
-  int32_t* d_out = nullptr;
-  int rc = GATSPI_OK;
-  std::vector<int32_t> cnt(N);
-  std::vector<uint8_t> iv(N);
-  std::vector<long long> dst(N);
-  int64_t tot = 0;
-  auto cleanup = [&]() { dfree(d_cnt); dfree(d_iv); dfree(d_dst); dfree(d_out); };
-  do {
-    if (cudaMalloc(&d_cnt, sizeof(int32_t) * N) != cudaSuccess || cudaMalloc(&d_iv, N) != cudaSuccess ||
-        cudaMalloc(&d_dst, sizeof(long long) * N) != cudaSuccess) {
-      cudaGetLastError();
-      rc = fail(ctx, GATSPI_ENOMEM, "read-back buffers");
-      break;
-    }
-    window_counts_kernel<<<(N + 255) / 256, 256, 0, ctx->stream>>>(N, ctx->batch_nw, w, ctx->d_rmeta, d_cnt,
-                                                                   d_iv);
-    if (cudaMemcpyAsync(cnt.data(), d_cnt, sizeof(int32_t) * N, cudaMemcpyDeviceToHost, ctx->stream) ||
-        cudaMemcpyAsync(iv.data(), d_iv, N, cudaMemcpyDeviceToHost, ctx->stream) ||
-        cudaStreamSynchronize(ctx->stream)) {
-      rc = fail(ctx, GATSPI_ECUDA, "read-back copy failed");
-      break;
-    }
-    // caller order
-    ptr[0] = 0;
-    for (int32_t e = 0; e < N; ++e) {
-      const int32_t n = ctx->net_int[e];
-      init[e] = iv[n];
-      ptr[e + 1] = ptr[e] + cnt[n];
-    }
-    tot = ptr[N];
-    if (total) *total = tot;
-    if (!times) break;
-    if (cap < tot) {
-      rc = fail(ctx, GATSPI_ECAPACITY, "times buffer too small: need " + std::to_string(tot));
-      break;
-    }
-    for (int32_t e = 0; e < N; ++e) dst[ctx->net_int[e]] = ptr[e];
-    if (cudaMalloc(&d_out, sizeof(int32_t) * std::max<int64_t>(tot, 1)) != cudaSuccess) {
-      cudaGetLastError();
-      rc = fail(ctx, GATSPI_ENOMEM, "read-back buffers");
-      break;
-    }
-    if (cudaMemcpyAsync(d_dst, dst.data(), sizeof(long long) * N, cudaMemcpyHostToDevice, ctx->stream)) {
-      rc = fail(ctx, GATSPI_ECUDA, "read-back copy failed");
-      break;
-    }
-    window_gather_kernel<<<(N + 255) / 256, 256, 0, ctx->stream>>>(N, ctx->batch_nw, w, ctx->d_net_level,
-                                                                   ctx->d_rstart, ctx->d_tinfo, ctx->batch_T,
-                                                                   ctx->batch_TW, ctx->d_rmeta, ctx->d_lvl_base,
-                                                                   ctx->d_times, d_dst, d_out);
-    if (cudaMemcpyAsync(times, d_out, sizeof(int32_t) * tot, cudaMemcpyDeviceToHost, ctx->stream) ||
-        cudaStreamSynchronize(ctx->stream)) {
-      rc = fail(ctx, GATSPI_ECUDA, "read-back copy failed");
-      break;
-    }
-  } while (0);
-  cleanup();
-  return rc;
+  return guarded(ctx, [&]() -> int {
+    if (!ctx) return GATSPI_EINVAL;
+    if (!ctx->have_result) return fail(ctx, GATSPI_ESTATE, "nothing simulated yet");
+    if (!init || !ptr) return fail(ctx, GATSPI_EINVAL, "null output array");
+    if (window < ctx->batch_w0 || window >= ctx->batch_w0 + ctx->batch_nw)
+      return fail(ctx, GATSPI_ESTATE, "window " + std::to_string(window) + " is not in the resident batch [" +
+                                          std::to_string(ctx->batch_w0) + ", " +
+                                          std::to_string(ctx->batch_w0 + ctx->batch_nw) + ")");
+    CK(cudaSetDevice(ctx->device));
+    const int32_t N = ctx->N, w = window - ctx->batch_w0;
+    int32_t* d_cnt = nullptr;
+    uint8_t* d_iv = nullptr;
+    long long* d_dst = nullptr;
+    int32_t* d_out = nullptr;
+    int rc = GATSPI_OK;
+    std::vector<int32_t> cnt(N);
+    std::vector<uint8_t> iv(N);
+    std::vector<long long> dst(N);
+    int64_t tot = 0;
+    auto cleanup = [&]() { dfree(d_cnt); dfree(d_iv); dfree(d_dst); dfree(d_out); };
+    do {
+      if (cudaMalloc(&d_cnt, sizeof(int32_t) * N) != cudaSuccess || cudaMalloc(&d_iv, N) != cudaSuccess ||
+          cudaMalloc(&d_dst, sizeof(long long) * N) != cudaSuccess) {
+        cudaGetLastError();
+        rc = fail(ctx, GATSPI_ENOMEM, "read-back buffers");
+        break;
+      }
+      window_counts_kernel<<<(N + 255) / 256, 256, 0, ctx->stream>>>(N, ctx->batch_nw, w, ctx->d_rmeta, d_cnt,
+                                                                     d_iv);
+      if (cudaMemcpyAsync(cnt.data(), d_cnt, sizeof(int32_t) * N, cudaMemcpyDeviceToHost, ctx->stream) ||
+          cudaMemcpyAsync(iv.data(), d_iv, N, cudaMemcpyDeviceToHost, ctx->stream) ||
+          cudaStreamSynchronize(ctx->stream)) {
+        rc = fail(ctx, GATSPI_ECUDA, "read-back copy failed");
+        break;
+      }
+      // caller order
+      ptr[0] = 0;
+      for (int32_t e = 0; e < N; ++e) {
+        const int32_t n = ctx->net_int[e];
+        init[e] = iv[n];
+        ptr[e + 1] = ptr[e] + cnt[n];
+      }
+      tot = ptr[N];
+      if (total) *total = tot;
+      if (!times) break;
+      if (cap < tot) {
+        rc = fail(ctx, GATSPI_ECAPACITY, "times buffer too small: need " + std::to_string(tot));
+        break;
+      }
+      for (int32_t e = 0; e < N; ++e) dst[ctx->net_int[e]] = ptr[e];
+      if (cudaMalloc(&d_out, sizeof(int32_t) * std::max<int64_t>(tot, 1)) != cudaSuccess) {
+        cudaGetLastError();
+        rc = fail(ctx, GATSPI_ENOMEM, "read-back buffers");
+        break;
+      }
+      if (cudaMemcpyAsync(d_dst, dst.data(), sizeof(long long) * N, cudaMemcpyHostToDevice, ctx->stream)) {
+        rc = fail(ctx, GATSPI_ECUDA, "read-back copy failed");
+        break;
+      }
+      window_gather_kernel<<<(N + 255) / 256, 256, 0, ctx->stream>>>(N, ctx->batch_nw, w, ctx->d_net_level,
+                                                                     ctx->d_rstart, ctx->d_tinfo, ctx->batch_T,
+                                                                     ctx->batch_TW, ctx->d_rmeta, ctx->d_lvl_base,
+                                                                     ctx->d_times, d_dst, d_out);
+      if (cudaMemcpyAsync(times, d_out, sizeof(int32_t) * tot, cudaMemcpyDeviceToHost, ctx->stream) ||
+          cudaStreamSynchronize(ctx->stream)) {
+        rc = fail(ctx, GATSPI_ECUDA, "read-back copy failed");
+        break;
+      }
+    } while (0);
+    cleanup();
+    return rc;
+  });
 }
 
 int gatspi_get_stats(gatspi_ctx* ctx, gatspi_stats* out) {
-  if (!ctx || !out) return GATSPI_EINVAL;
-  *out = ctx->stats;
-  return GATSPI_OK;
+  return guarded(ctx, [&]() -> int {
+    if (!ctx || !out) return GATSPI_EINVAL;
+    *out = ctx->stats;
+    return GATSPI_OK;
+  });
 }
 
 }  // extern "C"
