@@ -43,7 +43,10 @@ struct ENetlist {
 struct EJob {
   int64_t id = 0;
   int32_t net = 0, C = 0, L = 0, W = 1, n_windows = 0, max_edit = 0;
-  std::vector<int64_t> edge_ptr;
+  // each input's edges before cycle c (edge_ptr[i*C + c] for every input i),
+  // for the cycles where parts begin or end: all a part's planning needs,
+  // without a host copy of the whole edge_ptr
+  std::map<int32_t, std::vector<int64_t>> at_cycle;
   int64_t* d_edge_ptr = nullptr;
   int32_t* d_edge_time = nullptr;
   uint8_t* d_init_in = nullptr;
@@ -274,6 +277,41 @@ int stage_reserve(gatspi_engine* eng, size_t bytes) {
 }
 
 // Retire parts whose last level has finished on the device.
+// Each input's edges before cycle c of job j: captured at submission for
+// the planned part bounds; a bound made later (a part split in two) is
+// read from the job's device copy of edge_ptr, after its upload.
+int bounds_at(gatspi_engine* eng, EJob& j, int32_t c, const std::vector<int64_t>** out) {
+  auto it = j.at_cycle.find(c);
+  if (it == j.at_cycle.end()) {
+    ENetlist& nl = *eng->nets[j.net];
+    std::vector<int64_t> v(nl.r.I);
+    ECK(cudaMemcpy2DAsync(v.data(), sizeof(int64_t), j.d_edge_ptr + c, sizeof(int64_t) * (size_t)j.C,
+                          sizeof(int64_t), (size_t)nl.r.I, cudaMemcpyDeviceToHost, eng->upload));
+    ECK(cudaStreamSynchronize(eng->upload));
+    it = j.at_cycle.emplace(c, std::move(v)).first;
+  }
+  *out = &it->second;
+  return GATSPI_OK;
+}
+
+// Edges of all inputs in cycles [c0, c1) of job j, and optionally each
+// input's exclusive prefix of them.
+int batch_edges(gatspi_engine* eng, EJob& j, int32_t c0, int32_t c1, int64_t* l0, std::vector<long long>* pre) {
+  const std::vector<int64_t>* a = nullptr;
+  const std::vector<int64_t>* b = nullptr;
+  int rc = bounds_at(eng, j, c0, &a);
+  if (!rc) rc = bounds_at(eng, j, c1, &b);
+  if (rc) return rc;
+  int64_t s = 0;
+  if (pre) pre->resize(a->size());
+  for (size_t i = 0; i < a->size(); ++i) {
+    if (pre) (*pre)[i] = s;
+    s += (*b)[i] - (*a)[i];
+  }
+  *l0 = s;
+  return GATSPI_OK;
+}
+
 int retire(gatspi_engine* eng, bool wait_one) {
   bool waited = false;
   for (size_t k = 0; k < eng->finishing.size();) {
@@ -509,7 +547,6 @@ int gatspi_engine_submit(gatspi_engine* eng, int32_t netlist_id, int32_t num_cyc
     j->C = num_cycles; j->L = cycle_ps; j->W = W; j->max_edit = max_edit;
     j->n_windows = (num_cycles + W - 1) / W;
     const int64_t n = (int64_t)nl.r.I * num_cycles;
-    j->edge_ptr.assign(edge_ptr, edge_ptr + n + 1);
     int rc;
     auto undo = [&](int code) { free_job_device(*j, eng->stream); return code; };
     if ((rc = eupload_async(eng, j->d_edge_ptr, edge_ptr, (size_t)n + 1))) return undo(rc);
@@ -530,15 +567,22 @@ int gatspi_engine_submit(gatspi_engine* eng, int32_t netlist_id, int32_t num_cyc
     int64_t per = std::max<int64_t>(1, eng->opts.part_items / std::max<int64_t>(nl.r.N, 1));
     per = std::min<int64_t>(per, 0x7fff0000ll / widest);
     per = std::max<int64_t>(per, 1);
+    auto capture = [&](int32_t c) {  // the validated caller array, at cycle c
+      std::vector<int64_t>& v = j->at_cycle[c];
+      v.resize(nl.r.I);
+      for (int32_t i = 0; i < nl.r.I; ++i) v[i] = edge_ptr[(size_t)i * num_cycles + c];
+    };
     for (int32_t w0 = 0; w0 < j->n_windows; w0 += (int32_t)per) {
       std::unique_ptr<EPart> p(new EPart());
       p->job = j->id;
       p->D = nl.r.D;
       p->w0 = w0;
       p->nw = (int32_t)std::min<int64_t>(per, j->n_windows - w0);
+      capture(std::min(w0 * W, num_cycles));
       eng->queued.push_back(std::move(p));
       j->parts_total++;
     }
+    capture(num_cycles);
     *job_id = j->id;
     eng->jobs[j->id] = std::move(j);
     return GATSPI_OK;
@@ -570,8 +614,7 @@ static int engine_step_impl(gatspi_engine* eng, int32_t* active_out, int32_t* qu
       // level-0 edges are known; the rest follows the netlist's history
       const int32_t c0 = p.w0 * j.W, c1 = std::min((p.w0 + p.nw) * j.W, j.C);
       int64_t l0 = 0;
-      for (int32_t i = 0; i < nl.r.I; ++i)
-        l0 += j.edge_ptr[(size_t)i * j.C + c1] - j.edge_ptr[(size_t)i * j.C + c0];
+      if ((rc = batch_edges(eng, j, c0, c1, &l0, nullptr))) return rc;
       p.edge_hint = l0 + (int64_t)(nl.edges_per_item * (double)nl.r.G * p.nw * 1.25) + 4096;
     }
     const size_t bytes = part_layout(nl, p, eng->ipt, nullptr);
@@ -604,13 +647,10 @@ static int engine_step_impl(gatspi_engine* eng, int32_t* active_out, int32_t* qu
     eng->step_load += own->level_items;
     eng->stats.bytes_peak = std::max<int64_t>(eng->stats.bytes_peak, (int64_t)eng->in_use);
     ECK(cudaMemsetAsync(own->mem + own->zero_off, 0, own->zero_bytes, eng->stream));
-    std::vector<long long> pre(nl.r.I);
-    long long l0 = 0;
+    std::vector<long long> pre;
+    int64_t l0 = 0;
     const int32_t c0 = own->w0 * j.W, c1 = std::min((own->w0 + own->nw) * j.W, j.C);
-    for (int32_t i = 0; i < nl.r.I; ++i) {
-      pre[i] = l0;
-      l0 += j.edge_ptr[(size_t)i * j.C + c1] - j.edge_ptr[(size_t)i * j.C + c0];
-    }
+    if ((rc = batch_edges(eng, j, c0, c1, &l0, &pre))) return rc;
     prefixes.push_back(std::move(pre));
     own->level = 0;
     admitted.push_back(own.get());
@@ -697,10 +737,9 @@ static int engine_step_impl(gatspi_engine* eng, int32_t* active_out, int32_t* qu
     q.in_prefix = (const long long*)(eng->d_stage + pre_off[k]);
     q.rstart = p.rstart; q.tinfo = p.tinfo; q.T = p.T; q.TW = p.TW; q.rmeta = p.rmeta; q.times = p.times; q.saif_t1 = p.t1; q.saif_tc = p.tc;
     q.lvl_base = p.lvl_base; q.status = p.status;
-    long long l0 = 0;
+    int64_t l0 = 0;
     const int32_t c0 = p.w0 * j.W, c1 = std::min((p.w0 + p.nw) * j.W, j.C);
-    for (int32_t i = 0; i < nl.r.I; ++i)
-      l0 += j.edge_ptr[(size_t)i * j.C + c1] - j.edge_ptr[(size_t)i * j.C + c0];
+    if ((rc = batch_edges(eng, j, c0, c1, &l0, nullptr))) return rc;
     if (l0 > p.cap) {  // cannot happen: the hint covers level 0
       return fail_job(eng, j, GATSPI_ECAPACITY, "input edges exceed the part's store");
     }
