@@ -393,3 +393,28 @@ def test_digest_is_order_free_and_local():
     assert np.count_nonzero(moved != base) == 1 and moved[n] != base[n]
     # the window index enters: the same waveforms at another index differ
     assert not np.array_equal(odig.window_terms(init, ptr, times, 8), base)
+
+
+# ---------------------------------------------------------- time translation
+
+@pytest.mark.parametrize("pulse", [(100, 100), (0, 0), (40, 70)], ids=["g100w100", "g0w0", "g40w70"])
+def test_shifting_every_input_edge_shifts_every_waveform(pulse):
+    # nothing in the method depends on absolute time: moving all of a
+    # window's input edges later by d moves every net's edges later by d
+    # (start values unchanged), in both formulations
+    rng = np.random.Generator(np.random.PCG64(99))
+    for s in range(120):
+        wl = gen.random_small(40_000 + s, max_cycles=1)
+        st = wl.stim
+        d = int(rng.integers(1, 300))
+        big = st.cycle_ps + d + 10
+        shifted = gen.Stimulus(st.num_cycles, big, st.init, st.edge_ptr, (st.edge_time + d).astype(np.int32))
+        base = gen.Stimulus(st.num_cycles, big, st.init, st.edge_ptr, st.edge_time)
+        a = oracle.EventSim(wl.netlist, wl.delays, base, W=1, pulse_gate=pulse[0], pulse_wire=pulse[1])
+        b = oracle.EventSim(wl.netlist, wl.delays, shifted, W=1, pulse_gate=pulse[0], pulse_wire=pulse[1])
+        ia, pa, ta = a.window(0)
+        ib, pb, tb = b.window(0)
+        assert np.array_equal(ia, ib) and np.array_equal(pa, pb), f"case {s}"
+        assert np.array_equal(ta.astype(np.int64) + d, tb), f"case {s}"
+        a1 = algo1.simulate_window(wl.netlist, wl.delays, shifted, 0, 1, *pulse)
+        assert [(i, list(t)) for i, t in a1] == oracle.windows_as_lists(ib, pb, tb)
