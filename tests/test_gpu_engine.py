@@ -8,6 +8,7 @@ import pytest
 import gen
 import oracle
 import paper_2203_06117_gb300 as gs
+from helpers import edited_delays
 
 pytestmark = pytest.mark.gpu
 
@@ -15,18 +16,6 @@ pytestmark = pytest.mark.gpu
 @pytest.fixture(scope="module", autouse=True)
 def _built():
     gs.build()
-
-
-def edited_delays(nl, dl, gates, deltas):
-    """The delay table with a job's edit applied: every gate delay of an
-    edited gate shifted by its delta, clamped at 1 ps."""
-    gd = dl.gate_delay.copy().reshape(-1, 2, 2, 8)
-    for g, d in zip(gates, deltas):
-        a, b = int(nl.fanin_ptr[g]), int(nl.fanin_ptr[g + 1])
-        ncol = 1 << (b - a - 1)
-        blk = gd[a:b, :, :, :ncol]
-        gd[a:b, :, :, :ncol] = np.maximum(1, blk + int(d))
-    return gen.Delays(gd.reshape(-1), dl.wire_delay)
 
 
 def oracle_saif(nl, dl, st, W=1):

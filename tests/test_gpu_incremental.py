@@ -16,8 +16,7 @@ import gen
 import oracle
 from oracle import digest as odig
 import paper_2203_06117_gb300 as gs
-from test_gpu_engine import edited_delays
-from test_gpu_parity import assert_saif_equal, assert_window_equal
+from helpers import assert_saif_equal, assert_window_equal, edited_delays
 
 pytestmark = pytest.mark.gpu
 

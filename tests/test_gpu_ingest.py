@@ -16,7 +16,7 @@ import oracle
 from oracle import digest as odig
 from oracle import stimulus as ostim
 import paper_2203_06117_gb300 as gs
-from test_stimulus_io import parse_saif, write_vcd
+from helpers import parse_saif, write_vcd
 
 pytestmark = pytest.mark.gpu
 

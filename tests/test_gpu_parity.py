@@ -13,6 +13,7 @@ import gen
 import oracle
 import paper_2203_06117_gb300 as gs
 from cases import case_workload, load_hand_traced
+from helpers import assert_saif_equal, assert_window_equal
 
 pytestmark = pytest.mark.gpu
 
@@ -22,34 +23,6 @@ CASES = load_hand_traced()
 @pytest.fixture(scope="module", autouse=True)
 def _built():
     gs.build()
-
-
-def assert_window_equal(sim, ref, w, what=""):
-    gi, gp, gt = sim.window(w)
-    oi, op, ot = ref.window(w)
-    if not np.array_equal(gi, oi):
-        n = int(np.nonzero(gi != oi)[0][0])
-        raise AssertionError(f"{what} window {w}: start value of net {n}: gpu {gi[n]} oracle {oi[n]}")
-    if not (np.array_equal(gp, op) and np.array_equal(gt, ot)):
-        cg, co = np.diff(gp), np.diff(op)
-        bad = np.nonzero(cg != co)[0]
-        n = int(bad[0]) if bad.size else -1
-        if n < 0:
-            for m in range(gi.shape[0]):
-                if not np.array_equal(gt[gp[m]:gp[m + 1]], ot[op[m]:op[m + 1]]):
-                    n = m
-                    break
-        raise AssertionError(f"{what} window {w}: net {n}: gpu {gt[gp[n]:gp[n + 1]].tolist()} "
-                             f"oracle {ot[op[n]:op[n + 1]].tolist()}")
-
-
-def assert_saif_equal(sim, ref):
-    g = sim.saif()
-    o = ref.saif()
-    for name, a, b in zip(("T0", "T1", "TC"), g, o):
-        if not np.array_equal(a, b):
-            n = int(np.nonzero(a != b)[0][0])
-            raise AssertionError(f"SAIF {name} of net {n}: gpu {a[n]} oracle {b[n]}")
 
 
 @pytest.mark.parametrize("case", CASES, ids=[c["name"] for c in CASES])

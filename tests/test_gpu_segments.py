@@ -12,7 +12,7 @@ import pytest
 import gen
 import oracle
 import paper_2203_06117_gb300 as gs
-from test_gpu_parity import assert_window_equal
+from helpers import assert_window_equal
 
 pytestmark = pytest.mark.gpu
 

@@ -11,7 +11,6 @@
 * The library's SAIF writer's files parse back to the arrays written.
 """
 import os
-import re
 
 import numpy as np
 import pytest
@@ -19,6 +18,7 @@ import pytest
 import gen
 import paper_2203_06117_gb300 as gs
 from oracle import stimulus as ostim
+from helpers import parse_saif, write_vcd
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -71,56 +71,6 @@ def test_oracle_rejects_bad_events(inp, t):
 
 
 # -------------------------------------------------------------- VCD reader
-
-def _codes(k):
-    """VCD identifier codes: printable characters 33..126, several per code."""
-    out = []
-    for n in range(k):
-        s, n = "", n + 1
-        while n:
-            n, r = divmod(n - 1, 94)
-            s = chr(33 + r) + s
-        out.append(s)
-    return out
-
-
-def write_vcd(path, stim, names, unit="1ps", scope=("top",), glitch_every=0, alias=None):
-    """A VCD dump of a per-cycle stimulus (absolute times divided by the
-    unit's picoseconds, which must divide them)."""
-    ps = {"1ps": 1, "10ps": 10, "100ps": 100, "1ns": 1000, "1 ps": 1}[unit]
-    I = stim.init.size
-    codes = _codes(I)
-    inp, t = gs_events = ostim.cycles_to_events(stim)
-    assert np.all(t % ps == 0)
-    order = np.lexsort((inp, t))
-    lines = ["$date today $end", "$version writer in the tests $end", f"$timescale {unit} $end"]
-    for s in scope:
-        lines.append(f"$scope module {s} $end")
-    for k in range(I):
-        lines.append(f"$var wire 1 {codes[k]} {names[k]} $end")
-    if alias is not None:                      # a second name sharing input 0's code
-        lines.append(f"$var wire 1 {codes[0]} {alias} $end")
-    lines.append("$var wire 4 " + "%%" + " bus [3:0] $end")
-    for _ in scope:
-        lines.append("$upscope $end")
-    lines += ["$enddefinitions $end", "#0", "$dumpvars"]
-    lines += [f"{int(stim.init[k])}{codes[k]}" for k in range(I)] + ["b0000 %%", "$end"]
-    val = stim.init.astype(np.int64).copy()
-    cur = None
-    for j, e in enumerate(order):
-        tt, k = int(t[e]) // ps, int(inp[e])
-        if tt != cur:
-            lines.append(f"#{tt}")
-            cur = tt
-            if glitch_every and j % glitch_every == 0:
-                # a zero-width glitch on another input: two changes in one step
-                o = (k + 1) % I
-                lines += [f"{1 - val[o]}{codes[o]}", f"{val[o]}{codes[o]}"]
-        val[k] ^= 1
-        lines.append(f"{val[k]}{codes[k]}")
-    with open(path, "w") as f:
-        f.write("\n".join(lines) + "\n")
-
 
 def _check_vcd_round_trip(tmp_path, stim, **kw):
     names = [f"in{k}" for k in range(stim.init.size)]
@@ -220,17 +170,6 @@ def test_vcd_values_inside_one_step_count_by_their_last_value(tmp_path):
 
 
 # -------------------------------------------------------------- SAIF writer
-
-def parse_saif(path):
-    text = open(path).read()
-    head = dict(re.findall(r"\((DURATION|DESIGN|TIMESCALE) ([^)]*)\)", text))
-    nets = {}
-    for name, t0, t1, tx, tc, ig in re.findall(
-            r"\(((?:\\.|[A-Za-z0-9_])+)\s*\(T0 (\d+)\) \(T1 (\d+)\) \(TX (\d+)\)\s*\(TC (\d+)\) \(IG (\d+)\)",
-            text):
-        nets[re.sub(r"\\(.)", r"\1", name)] = (int(t0), int(t1), int(tx), int(tc), int(ig))
-    return head, nets
-
 
 def test_saif_file_round_trip(tmp_path):
     rng = np.random.Generator(np.random.PCG64(2))
