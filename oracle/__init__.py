@@ -34,7 +34,7 @@ MUTATIONS = {
     "gate_cancel_on_equal": 3, "msi_lowest_pin": 4, "side_before_switch": 5,
     "row_transposed": 6, "t1_unclipped": 7, "window_init_from_cycle0": 8,
     "no_wire_filter": 9, "no_gate_filter": 10, "out_delay_from_old_y": 11,
-    "gate_stack_depth_one": 12, "wire_crossing_kept": 13,
+    "gate_stack_depth_one": 12, "wire_crossing_kept": 13, "side_low_bits": 14,
 }
 
 

@@ -94,7 +94,8 @@ enum {
   M_NO_GATE_FILTER = 10,
   M_OUT_DELAY_FROM_OLD_Y = 11,
   M_GATE_STACK_DEPTH_ONE = 12,
-  M_WIRE_CROSSING_KEPT = 13
+  M_WIRE_CROSSING_KEPT = 13,
+  M_SIDE_LOW_BITS = 14
 };
 
 typedef struct { uint64_t key; int64_t seq; } event_t;
@@ -379,6 +380,10 @@ static int gate_eval(osim_t* s, int32_t g, int32_t t, int istar, uint32_t col_be
   int out_edge = y;
   if (s->mutation == M_OUT_DELAY_FROM_OLD_Y) out_edge = s->vs[g];
   uint32_t side = side_column(s->mutation == M_SIDE_BEFORE_SWITCH ? col_before : col, istar);
+  if (s->mutation == M_SIDE_LOW_BITS) {
+    int npins = s->fanin_ptr[g + 1] - s->fanin_ptr[g];
+    side = col & ((1u << (npins - 1)) - 1u);
+  }
   int row = s->mutation == M_ROW_TRANSPOSED ? (2 * out_edge + in_edge) : (2 * in_edge + out_edge);
   int32_t d = s->gate_delay[(int64_t)p * 32 + row * 8 + side];
   int64_t top = s->last_seq[g];
