@@ -321,8 +321,11 @@ int gatspi_get_stats(gatspi_ctx* ctx, gatspi_stats* out);
  * Several changes of one signal in one time step count only by their final
  * value (a zero-width glitch is no toggle).  Supported:
  * $timescale of 1, 10 or 100 s, ms, us, ns or ps; $scope/$upscope; scalar
- * changes and 1-bit vectors ("b1 id"); $dumpvars and the like.  Values x/z
- * of a requested signal are rejected (2-value simulation, Section 2).
+ * changes and 1-bit vectors ("b1 id"); $dumpvars, $dumpall and $dumpon
+ * blocks (ordinary changes) and $dumpoff blocks (their x values are
+ * ignored; the values after $dumpon count as changes at that time).
+ * Other x/z values of a requested signal are rejected (2-value
+ * simulation, Section 2).
  * `cap` is the size of ev_input / ev_time; *num_events receives the total.
  * Errors: EINVAL (file, syntax, names, x/z, a first value after time 0),
  * ECAPACITY (cap < total: call again with larger arrays).  A message goes

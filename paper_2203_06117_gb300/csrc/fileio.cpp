@@ -177,9 +177,11 @@ int vcd_read(const char* path, int32_t num_names, const char* const* names, uint
     }
     touched.clear();
   };
+  bool dump_off = false;  // inside a $dumpoff block: its (x) values are not changes
   auto change = [&](char v, const std::string& code) -> int {
     auto it = code_inputs.find(code);
     if (it == code_inputs.end()) return GATSPI_OK;  // not an input of interest
+    if (dump_off) return GATSPI_OK;
     if (v != '0' && v != '1') {
       say(err, err_len, std::string("value '") + v + "' at time " + std::to_string(now) +
                             ": the simulation is 2-valued (0/1)");
@@ -235,10 +237,17 @@ int vcd_read(const char* path, int32_t num_names, const char* const* names, uint
       now = t;
       have_time = true;
     } else if (c0 == '$') {
-      // $dumpvars / $dumpall / $dumpon / $dumpoff / $end: value changes
-      // inside them count as ordinary changes; other commands are skipped
+      // $dumpvars / $dumpall / $dumpon / $end: value changes inside them
+      // count as ordinary changes.  $dumpoff lists every variable as x
+      // until its $end: those are no changes (the waveform is not dumped
+      // until $dumpon, whose values then count as changes at its time).
+      // Other commands are skipped.
       if (tok == "$comment") {
         while (tk.next(tok) && tok != "$end") {}
+      } else if (tok == "$dumpoff") {
+        dump_off = true;
+      } else if (tok == "$end") {
+        dump_off = false;
       }
     } else if (c0 == '0' || c0 == '1' || c0 == 'x' || c0 == 'X' || c0 == 'z' || c0 == 'Z') {
       int rc = change(c0, tok.substr(1));

@@ -187,3 +187,16 @@ def test_saif_file_round_trip(tmp_path):
         assert nets[nm] == (total - int(t1[k]), int(t1[k]), 0, int(tc[k]), 0)
     text = open(p).read()
     assert r"u1\/a\[3\]" in text and r"weird\ name" in text and r"x\(1\)" in text
+
+
+def test_vcd_dumpoff_blocks_are_not_changes(tmp_path):
+    p = os.path.join(tmp_path, "off.vcd")
+    with open(p, "w") as f:
+        f.write("$timescale 1ps $end $var wire 1 ! a $end $var wire 1 # b $end $enddefinitions $end "
+                "#0 $dumpvars 0! 1# $end #10 1! #20 $dumpoff x! x# $end #50 $dumpon 0! 1# $end "
+                "#60 0#\n")
+    init, ei, et = gs.gatspi_vcd_read(p, ["a", "b"])
+    # a: 0, rises at 10, the dump is off 20-50, back on at 50 with a = 0:
+    # a toggle at 50; b: 1 throughout the gap, falls at 60
+    assert init.tolist() == [0, 1]
+    assert list(zip(ei.tolist(), et.tolist())) == [(0, 10), (0, 50), (1, 60)]
