@@ -499,7 +499,14 @@ int gatspi_engine_get_stats(gatspi_engine* eng, gatspi_engine_stats* out);
  * call's contents (each call clears it first): calls that may overlap on
  * the GPU -- on different streams without ordering -- race and give wrong
  * results.  Levels of one job must run in order anyway.
- * Errors: EINVAL (null pointer, bad range), ECAPACITY (more than
+ * Window w of the batch is global window first_window + w, cycles
+ * [(first_window + w) * window_cycles, ...) clipped to num_cycles, on its own
+ * time axis; first_window + num_windows must not exceed ceil(num_cycles /
+ * window_cycles).  Every time is int32 ps: the caller must keep the window
+ * length (window_cycles * cycle_ps) plus the longest path delay below 2^31
+ * (the window length alone is checked).
+ * Errors: EINVAL (null pointer, bad range, windows past the stimulus,
+ * window length of 2^31 ps or more), ECAPACITY (more than
  * GATSPI_NOALLOC_MAX_ITEMS (gate, window) items in the level: use fewer
  * windows per call), ECUDA.  A message is written to err/err_len when given.
  * ---------------------------------------------------------------------- */

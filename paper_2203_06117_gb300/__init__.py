@@ -29,7 +29,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libgatspi.so")
 INCLUDE = os.path.join(ROOT, "include")
 SOURCES = [os.path.join(_HERE, "csrc", f) for f in ("gatspi.cu", "engine.cu", "noalloc.cu", "fileio.cpp")]
 DEPS = SOURCES + [os.path.join(_HERE, "csrc", f) for f in ("kernels.cuh", "digest.cuh", "ingest.cuh",
-                                                           "host_common.h")] + \
+                                                           "host_common.h", "per_device.h")] + \
     [os.path.join(INCLUDE, "gatspi.h")]
 
 NVCC_FLAGS = ["-Xcompiler", "-fPIC", "-std=c++17",

@@ -723,6 +723,9 @@ static int engine_step_impl(gatspi_engine* eng, int32_t* active_out, int32_t* qu
       m.tile_counter = eng->d_counter + c;
       MultiLaunch go{&m, eng->stream};
       launch_variant(eng->nt, eng->ipt, go);
+      if (go.err)
+        return efail(eng, GATSPI_ECUDA, "enabling the propagation kernel's shared memory on device " +
+                                            std::to_string(eng->device) + " failed: " + cudaGetErrorString(go.err));
       ECK(cudaGetLastError());
       eng->stats.kernel_launches++;
     }

@@ -141,6 +141,11 @@ int fail(gatspi_ctx* c, int code, const std::string& msg) {
   return code;
 }
 
+std::string smem_message(int device, cudaError_t e) {
+  return "enabling the propagation kernel's shared memory on device " + std::to_string(device) +
+         " failed: " + cudaGetErrorString(e);
+}
+
 // Entry points run their bodies through this: a C++ exception (a host
 // allocation sized by the caller's input, a string operation) must not
 // cross the C interface; it becomes a status and a message instead.
@@ -714,6 +719,7 @@ int simulate_impl(gatspi_ctx* ctx, const gatspi_opts* opts) {
     }
     for (int32_t i = 0; i < ctx->I; ++i) ctx->h_in_prefix[i] = in_prefix[i];
     const bool record_first = o.time_kernels && !first_recorded;
+    cudaError_t smem_err = cudaSuccess;  // a propagation kernel could not opt in to its shared memory
     // everything the batch puts on the stream; captured into a CUDA graph
     // and replayed when the same batch comes again (repeated simulations of
     // one stimulus), launched eagerly otherwise.  Timing events are recorded
@@ -758,9 +764,15 @@ int simulate_impl(gatspi_ctx* ctx, const gatspi_opts* opts) {
         if (pp) {
           SingleLaunchMode<kModePulse> go{&p, ctx->stream};
           launch_variant_pp(nt, ipt, go);
+          e = go.err;
         } else {
           SingleLaunch go{&p, ctx->stream};
           launch_variant(nt, ipt, go);
+          e = go.err;
+        }
+        if (e) {
+          smem_err = e;
+          return e;
         }
         if ((e = cudaGetLastError())) return e;
         if (o.time_kernels && (e = rec(ctx->ev[2 * l + 1]))) return e;
@@ -817,7 +829,9 @@ int simulate_impl(gatspi_ctx* ctx, const gatspi_opts* opts) {
       }
     }
     if (!done) {
-      CK(enqueue(false));
+      const cudaError_t ee = enqueue(false);
+      if (ee && smem_err) return fail(ctx, GATSPI_ECUDA, smem_message(ctx->device, smem_err));
+      CK(ee);
       ctx->eager_nt = nt;
       ctx->eager_ipt = ipt;
       ctx->eager_pp = pp;
@@ -1099,13 +1113,17 @@ int gatspi_resimulate_edit(gatspi_ctx* ctx, int32_t n_edits, const int32_t* edit
       p.seg.append_in = ctx->d_append + (k & 1);
       p.seg.append_out = ctx->d_append + ((k + 1) & 1);
       p.tile_counter = ctx->d_tile_counter + l;
+      cudaError_t le = cudaSuccess;
       if (pp) {
         SingleLaunchMode<kModePulse> go{&p, ctx->stream};
         launch_variant_pp(nt, ipt, go);
+        le = go.err;
       } else {
         SingleLaunchMode<kModeCone> go{&p, ctx->stream};
         launch_variant_cone(ipt, go);
+        le = go.err;
       }
+      if (le) return fail(ctx, GATSPI_ECUDA, smem_message(ctx->device, le));
       CK(cudaGetLastError());
       ++k;
       ++r.levels;

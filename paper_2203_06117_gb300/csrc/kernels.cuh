@@ -34,6 +34,8 @@
 
 #include <cstdint>
 
+#include "per_device.h"
+
 namespace gatspi_dev {
 namespace {  // every translation unit gets its own copy of the kernels
 
@@ -1286,19 +1288,34 @@ inline long long level_tiles(long long gates, int32_t nw, int ipt) {
 template <int NT, int IPT>
 inline size_t dyn_smem() { return sizeof(WarpSmem<IPT>) * (NT / 32); }
 
+// Opts a kernel in to more than 48 KB of dynamic shared memory on the
+// current device.  The attribute belongs to the kernel on one device, so it
+// is set once per (kernel, device); `once` is the kernel's flag set.  On a
+// failure the error is returned (and stays the runtime's last error) and
+// the flag stays clear, so a later launch tries again.
+template <class Kern>
+inline cudaError_t smem_opt_in(Kern kern, size_t bytes, gatspi_host::PerDeviceOnce& once) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  once.run(dev, [&] {
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    return e == cudaSuccess ? 0 : 1;
+  });
+  return e;
+}
+
 // Host-side launchers of the two propagation kernels for one compiled
-// (threads, items per thread) variant.
+// (threads, items per thread) variant.  `err` holds the failure to opt in
+// to the variant's shared memory, if any (the kernel is then not launched).
 struct SingleLaunch {
   const PropParams* p;
   cudaStream_t s;
+  cudaError_t err = cudaSuccess;
   template <int NT, int IPT>
   void go() {
-    static bool attr = false;  // opt in to more than 48 KB of dynamic shared memory once
-    if (!attr) {
-      cudaFuncSetAttribute(propagate_kernel<NT, IPT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)dyn_smem<NT, IPT>());
-      attr = true;
-    }
+    static gatspi_host::PerDeviceOnce once;
+    if ((err = smem_opt_in(propagate_kernel<NT, IPT>, dyn_smem<NT, IPT>(), once)) != cudaSuccess) return;
     const unsigned grid = (unsigned)((p->seg.n_tiles + NT / 32 - 1) / (NT / 32));
     propagate_kernel<NT, IPT><<<grid, NT, dyn_smem<NT, IPT>(), s>>>(*p);
   }
@@ -1309,14 +1326,11 @@ template <int MODE>
 struct SingleLaunchMode {
   const PropParams* p;
   cudaStream_t s;
+  cudaError_t err = cudaSuccess;
   template <int NT, int IPT>
   void go() {
-    static bool attr = false;
-    if (!attr) {
-      cudaFuncSetAttribute(propagate_kernel<NT, IPT, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)dyn_smem<NT, IPT>());
-      attr = true;
-    }
+    static gatspi_host::PerDeviceOnce once;
+    if ((err = smem_opt_in(propagate_kernel<NT, IPT, MODE>, dyn_smem<NT, IPT>(), once)) != cudaSuccess) return;
     const unsigned grid = (unsigned)((p->seg.n_tiles + NT / 32 - 1) / (NT / 32));
     propagate_kernel<NT, IPT, MODE><<<grid, NT, dyn_smem<NT, IPT>(), s>>>(*p);
   }
@@ -1352,14 +1366,11 @@ inline bool launch_variant_cone(int ipt, SingleLaunchMode<kModeCone>& launch) {
 struct MultiLaunch {
   const MultiParams* m;
   cudaStream_t s;
+  cudaError_t err = cudaSuccess;
   template <int NT, int IPT>
   void go() {
-    static bool attr = false;
-    if (!attr) {
-      cudaFuncSetAttribute(propagate_multi_kernel<NT, IPT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)dyn_smem<NT, IPT>());
-      attr = true;
-    }
+    static gatspi_host::PerDeviceOnce once;
+    if ((err = smem_opt_in(propagate_multi_kernel<NT, IPT>, dyn_smem<NT, IPT>(), once)) != cudaSuccess) return;
     const unsigned grid = (unsigned)((m->n_tiles + NT / 32 - 1) / (NT / 32));
     propagate_multi_kernel<NT, IPT><<<grid, NT, dyn_smem<NT, IPT>(), s>>>(*m);
   }

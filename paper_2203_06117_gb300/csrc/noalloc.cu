@@ -82,6 +82,14 @@ extern "C" int gatspi_propagate_level_noalloc(const gatspi_level_args* a, void* 
       a->num_windows < 1 || a->first_window < 0 || a->window_cycles < 1 || a->num_cycles < 1 ||
       a->cycle_ps < 1 || a->capacity < 0)
     return say(a, GATSPI_EINVAL, "bad level, gate range, window or cycle argument");
+  // the windows must exist, and every window-relative time must stay below
+  // 2^31 (the caller keeps the window length plus the longest path delay
+  // below that; the window length alone is checked here)
+  const long long n_all = ((long long)a->num_cycles + a->window_cycles - 1) / a->window_cycles;
+  if ((long long)a->first_window + a->num_windows > n_all)
+    return say(a, GATSPI_EINVAL, "first_window + num_windows exceeds the stimulus' windows");
+  if ((long long)a->window_cycles * a->cycle_ps >= 0x80000000ll)
+    return say(a, GATSPI_EINVAL, "window_cycles * cycle_ps must stay below 2^31 ps");
   const long long items = (long long)(a->gate_end - a->gate_begin) * a->num_windows;
   if (items > GATSPI_NOALLOC_MAX_ITEMS)
     return say(a, GATSPI_ECAPACITY,
@@ -125,6 +133,8 @@ extern "C" int gatspi_propagate_level_noalloc(const gatspi_level_args* a, void* 
   p.tile_counter = (int32_t*)(scratch + 1);
   SingleLaunch go{&p, s};
   go.go<kNoAllocThreads, kNoAllocItemsPerThread>();
+  if (go.err != cudaSuccess)
+    return say(a, GATSPI_ECUDA, "enabling the propagation kernel's shared memory on this device failed");
   if (cudaGetLastError() != cudaSuccess) return say(a, GATSPI_ECUDA, "kernel launch failed");
   return GATSPI_OK;
 }
