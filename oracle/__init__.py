@@ -27,7 +27,10 @@ from . import algo1  # noqa: F401
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SO = os.path.join(_HERE, "_build", "liboracle.so")
-_lib = None
+# test-only build of the same file with the planted-mistake switches compiled
+# in (OSIM_PLANTED_MISTAKES); the oracle itself is built without them
+_SO_PLANTED = os.path.join(_HERE, "_build", "liboracle_planted.so")
+_libs = {}
 
 MUTATIONS = {
     "none": 0, "wire_rise_fall_swapped": 1, "wire_cancel_on_equal": 2,
@@ -38,21 +41,23 @@ MUTATIONS = {
 }
 
 
-def build(force: bool = False) -> str:
-    """Compile event_sim.c with the host C compiler."""
+def build(force: bool = False, planted: bool = False) -> str:
+    """Compile event_sim.c with the host C compiler (``planted``: the
+    test-only build with the planted-mistake switches)."""
     src = os.path.join(_HERE, "event_sim.c")
-    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(src):
-        os.makedirs(os.path.dirname(_SO), exist_ok=True)
-        tmp = _SO + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-std=c11", "-o", tmp, src])
-        os.replace(tmp, _SO)
-    return _SO
+    so = _SO_PLANTED if planted else _SO
+    if force or not os.path.exists(so) or os.path.getmtime(so) < os.path.getmtime(src):
+        os.makedirs(os.path.dirname(so), exist_ok=True)
+        tmp = so + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-std=c11", *(
+            ["-DOSIM_PLANTED_MISTAKES"] if planted else []), "-o", tmp, src])
+        os.replace(tmp, so)
+    return so
 
 
-def _load():
-    global _lib
-    if _lib is None:
-        lib = ctypes.CDLL(build())
+def _load(planted: bool = False):
+    if planted not in _libs:
+        lib = ctypes.CDLL(build(planted=planted))
         vp, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
         lib.osim_create.restype = vp
         lib.osim_create.argtypes = [i32, i32, vp, vp, vp, vp, vp, i32, i32, vp, vp, vp, i32, i32]
@@ -70,8 +75,10 @@ def _load():
         lib.osim_saif.argtypes = [vp, i32, i32, vp, vp]
         lib.osim_set_pulse.restype = i32
         lib.osim_set_pulse.argtypes = [vp, i32, i32]
-        _lib = lib
-    return _lib
+        lib.osim_set_full_sdf.restype = i32
+        lib.osim_set_full_sdf.argtypes = [vp, i32]
+        _libs[planted] = lib
+    return _libs[planted]
 
 
 def _p(a):
@@ -86,11 +93,26 @@ class EventSim:
     ``pulse_wire`` are the pulse limits (PATHPULSEPERCENT, 0..100) of the
     gate and interconnect inertial tests; 100 is Algorithm 1 as printed,
     0 transport delay (Section 3: other values edit the output test).
+
+    The two features the paper switches off to measure their cost (Section
+    5, Table "features"):
+    ``interconnect_filter=False`` deletes Algorithm 1's interconnect test;
+    arrivals of one pin that would cross or coincide still cancel as a pair,
+    which keeps each pin's arrivals in time order as Algorithm 1 assumes (the
+    same as an interconnect pulse limit of 0 percent).
+    ``full_sdf=False`` replaces each arc's table by its average rise and
+    fall delay over all COND columns and both input edges (osim_set_full_sdf).
+    ``mutation`` selects a planted mistake of the test-only build.
     """
 
     def __init__(self, netlist, delays, stim, W: int = 1, mutation: str = "none",
-                 pulse_gate: int = 100, pulse_wire: int = 100):
-        self._lib = _load()
+                 pulse_gate: int = 100, pulse_wire: int = 100, interconnect_filter: bool = True,
+                 full_sdf: bool = True):
+        if not interconnect_filter:
+            if pulse_wire != 100:
+                raise ValueError("oracle: interconnect_filter=False sets the interconnect limit itself")
+            pulse_wire = 0
+        self._lib = _load(planted=mutation != "none")
         # keep contiguous copies alive for the lifetime of the C object
         self._arrs = [np.ascontiguousarray(a) for a in (
             netlist.fanin_ptr.astype(np.int32), netlist.fanin_net.astype(np.int32),
@@ -109,6 +131,8 @@ class EventSim:
             raise ValueError("oracle: invalid netlist or stimulus")
         if self._lib.osim_set_pulse(self._h, int(pulse_gate), int(pulse_wire)) != 0:
             raise ValueError("oracle: pulse limits must be 0..100 percent")
+        if self._lib.osim_set_full_sdf(self._h, 1 if full_sdf else 0) != 0:
+            raise MemoryError("oracle: averaged delay table")
 
     def __del__(self):
         h = getattr(self, "_h", None)

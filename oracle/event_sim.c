@@ -79,7 +79,10 @@
 enum { K_ARRIVAL = 0, K_NETEDGE = 1 };
 
 /* Planted-mistake switches, used only by the test that checks the pins'
-   sensitivity; 0 in every other use. */
+   sensitivity.  They exist only in a separate test build compiled with
+   OSIM_PLANTED_MISTAKES (liboracle_planted.so); in the oracle itself every
+   #ifdef OSIM_PLANTED_MISTAKES block below is compiled out and osim_create
+   rejects a mistake number other than 0. */
 enum {
   M_NONE = 0,
   M_WIRE_RISE_FALL_SWAPPED = 1,
@@ -104,6 +107,8 @@ typedef struct {
   int32_t I, G, N, P, C, L, W, mutation;
   int32_t pulse_gate, pulse_wire;  /* pulse limits, percent of the delay */
   const int32_t *fanin_ptr, *fanin_net, *gate_delay, *wire_delay, *edge_time;
+  const int32_t* caller_gate_delay;  /* the table passed in (gate_delay may point at avg_delay) */
+  int32_t* avg_delay;                /* arcs averaged over COND columns and input edges, or NULL */
   const uint16_t* lut;
   const uint8_t* init;
   const int64_t* edge_ptr;
@@ -141,10 +146,13 @@ static int grow(void** p, int64_t* cap, int64_t need, size_t elem) {
   return 0;
 }
 
-/* At equal times arrivals sort before net edges; the planted mistake
-   M_WIRE_CANCEL_ON_EQUAL reverses that order as well. */
+/* At equal times arrivals sort before net edges. */
 static int kind_bit(const osim_t* s, int kind) {
-  return s->mutation == M_WIRE_CANCEL_ON_EQUAL ? !kind : kind;
+#ifdef OSIM_PLANTED_MISTAKES
+  if (s->mutation == M_WIRE_CANCEL_ON_EQUAL) return !kind;  /* net edges first */
+#endif
+  (void)s;
+  return kind;
 }
 
 static uint64_t mkkey(const osim_t* s, int32_t t, int kind, int32_t id) {
@@ -214,6 +222,7 @@ API void osim_destroy(osim_t* s) {
   free(s->heap); free(s->cancelled); free(s->below); free(s->seq_time);
   free(s->log_net); free(s->log_time);
   free(s->res_init); free(s->res_ptr); free(s->res_times); free(s->res_t1);
+  free(s->avg_delay);
   free(s);
 }
 
@@ -232,6 +241,9 @@ API osim_t* osim_create(int32_t I, int32_t G, const int32_t* fanin_ptr,
                         const int64_t* edge_ptr, const int32_t* edge_time,
                         int32_t W, int32_t mutation) {
   if (I < 0 || G < 0 || C < 0 || L < 1 || W < 1) return NULL;
+#ifndef OSIM_PLANTED_MISTAKES
+  if (mutation != M_NONE) return NULL;
+#endif
   osim_t* s = (osim_t*)calloc(1, sizeof(osim_t));
   if (!s) return NULL;
   s->I = I; s->G = G; s->N = I + G; s->C = C; s->L = L; s->W = W;
@@ -240,6 +252,7 @@ API osim_t* osim_create(int32_t I, int32_t G, const int32_t* fanin_ptr,
   s->pulse_wire = 100;
   s->fanin_ptr = fanin_ptr; s->fanin_net = fanin_net; s->lut = lut;
   s->gate_delay = gate_delay; s->wire_delay = wire_delay;
+  s->caller_gate_delay = gate_delay;
   s->init = init; s->edge_ptr = edge_ptr; s->edge_time = edge_time;
   s->P = G ? fanin_ptr[G] : 0;
   int32_t N = s->N, P = s->P;
@@ -296,6 +309,46 @@ API int32_t osim_set_pulse(osim_t* s, int32_t gate_percent, int32_t wire_percent
   return 0;
 }
 
+/*
+ * Full SDF delays (1, the default) or the partial-SDF variant of the
+ * paper's feature comparison (0; Section 5, Table "features"): every
+ * input-pin-to-output arc keeps only an average rise and an average fall
+ * delay of the output, each the mean of the arc's delays over all COND
+ * columns and both input edges, rounded to the nearest ps (halves up).  The
+ * averaged values replace the whole table of the arc, so the simulation
+ * itself is unchanged.  Returns 0, or -1 on a bad value or no memory.
+ */
+API int32_t osim_set_full_sdf(osim_t* s, int32_t full) {
+  if (full != 0 && full != 1) return -1;
+  if (full) {
+    s->gate_delay = s->caller_gate_delay;
+    return 0;
+  }
+  if (!s->avg_delay) {
+    s->avg_delay = (int32_t*)malloc(sizeof(int32_t) * 32 * (size_t)(s->P + 1));
+    if (!s->avg_delay) return -1;
+  }
+  for (int32_t g = 0; g < s->G; ++g) {
+    const int32_t n = s->fanin_ptr[g + 1] - s->fanin_ptr[g];
+    const int32_t ncol = 1 << (n - 1);
+    for (int32_t p = s->fanin_ptr[g]; p < s->fanin_ptr[g + 1]; ++p) {
+      const int32_t* d = s->caller_gate_delay + (int64_t)p * 32;
+      int32_t* a = s->avg_delay + (int64_t)p * 32;
+      for (int out_edge = 0; out_edge < 2; ++out_edge) {
+        int64_t sum = 0;
+        for (int in_edge = 0; in_edge < 2; ++in_edge)
+          for (int32_t c = 0; c < ncol; ++c) sum += d[(2 * in_edge + out_edge) * 8 + c];
+        const int64_t cnt = 2 * (int64_t)ncol;
+        const int32_t avg = (int32_t)((sum + cnt / 2) / cnt);
+        for (int in_edge = 0; in_edge < 2; ++in_edge)
+          for (int32_t c = 0; c < 8; ++c) a[(2 * in_edge + out_edge) * 8 + c] = avg;
+      }
+    }
+  }
+  s->gate_delay = s->avg_delay;
+  return 0;
+}
+
 API int32_t osim_num_windows(const osim_t* s) {
   return (s->C + s->W - 1) / s->W;
 }
@@ -334,23 +387,30 @@ static int net_edge(osim_t* s, int32_t n, int32_t t) {
   int rising = s->netval[n];
   for (int32_t k = s->fo_ptr[n]; k < s->fo_ptr[n + 1]; ++k) {
     int32_t p = s->fo_pin[k];
-    int use_rise = rising;
-    if (s->mutation == M_WIRE_RISE_FALL_SWAPPED) use_rise = !rising;
-    int32_t delta = use_rise ? s->wire_delay[2 * p] : s->wire_delay[2 * p + 1];
+    int32_t delta = rising ? s->wire_delay[2 * p] : s->wire_delay[2 * p + 1];
+#ifdef OSIM_PLANTED_MISTAKES
+    if (s->mutation == M_WIRE_RISE_FALL_SWAPPED) delta = rising ? s->wire_delay[2 * p + 1] : s->wire_delay[2 * p];
+#endif
     /* the pin's latest edge was kept and its arrival is still ahead */
-    int pending = s->arr_seq[p] != NONE &&
-                  (s->mutation == M_WIRE_CANCEL_ON_EQUAL ? s->arr_time[p] >= t
-                                                         : s->arr_time[p] > t);
+    int pending = s->arr_seq[p] != NONE && s->arr_time[p] > t;
+#ifdef OSIM_PLANTED_MISTAKES
+    if (s->mutation == M_WIRE_CANCEL_ON_EQUAL) pending = s->arr_seq[p] != NONE && s->arr_time[p] >= t;
     if (s->mutation == M_NO_WIRE_FILTER) pending = 0;
+#endif
     int drop = 0;
     if (pending) {
       /* the pulse (latest edge, this edge) is narrower than the limit, or
          would arrive with zero or negative width; at 100 percent every
          pending arrival qualifies, since pending means t - t_prev < delta */
       int64_t width = (int64_t)t - s->arr_src[p];
-      int crossed = (int64_t)t + delta <= s->arr_time[p] && s->mutation != M_WIRE_CROSSING_KEPT;
-      drop = 100 * width < (int64_t)s->pulse_wire * s->arr_delay[p] || crossed ||
-             s->mutation == M_WIRE_CANCEL_ON_EQUAL;
+      int crossed = (int64_t)t + delta <= s->arr_time[p];
+#ifdef OSIM_PLANTED_MISTAKES
+      if (s->mutation == M_WIRE_CROSSING_KEPT) crossed = 0;
+#endif
+      drop = 100 * width < (int64_t)s->pulse_wire * s->arr_delay[p] || crossed;
+#ifdef OSIM_PLANTED_MISTAKES
+      if (s->mutation == M_WIRE_CANCEL_ON_EQUAL) drop = 1;
+#endif
     }
     if (drop) {
       /* the pulse vanishes: cancel the earlier edge's arrival, schedule
@@ -378,13 +438,16 @@ static int gate_eval(osim_t* s, int32_t g, int32_t t, int istar, uint32_t col_be
   int32_t p = s->fanin_ptr[g] + istar;
   int in_edge = s->pinval[p];
   int out_edge = y;
-  if (s->mutation == M_OUT_DELAY_FROM_OLD_Y) out_edge = s->vs[g];
-  uint32_t side = side_column(s->mutation == M_SIDE_BEFORE_SWITCH ? col_before : col, istar);
-  if (s->mutation == M_SIDE_LOW_BITS) {
-    int npins = s->fanin_ptr[g + 1] - s->fanin_ptr[g];
-    side = col & ((1u << (npins - 1)) - 1u);
-  }
-  int row = s->mutation == M_ROW_TRANSPOSED ? (2 * out_edge + in_edge) : (2 * in_edge + out_edge);
+  uint32_t side = side_column(col, istar);
+  int row = 2 * in_edge + out_edge;
+#ifdef OSIM_PLANTED_MISTAKES
+  if (s->mutation == M_OUT_DELAY_FROM_OLD_Y) row = 2 * in_edge + s->vs[g];
+  if (s->mutation == M_SIDE_BEFORE_SWITCH) side = side_column(col_before, istar);
+  if (s->mutation == M_SIDE_LOW_BITS) side = col & ((1u << (s->fanin_ptr[g + 1] - s->fanin_ptr[g] - 1)) - 1u);
+  if (s->mutation == M_ROW_TRANSPOSED) row = 2 * out_edge + in_edge;
+#else
+  (void)col_before;
+#endif
   int32_t d = s->gate_delay[(int64_t)p * 32 + row * 8 + side];
   int64_t top = s->last_seq[g];
   int cancel = 0;
@@ -394,15 +457,21 @@ static int gate_eval(osim_t* s, int32_t g, int32_t t, int istar, uint32_t col_be
     int64_t E = s->last_time[g];
     int64_t to = (int64_t)t + d;
     cancel = 100 * (to - E) < (int64_t)s->pulse_gate * d || to <= E;
+#ifdef OSIM_PLANTED_MISTAKES
     if (s->mutation == M_GATE_CANCEL_ON_EQUAL) cancel = E >= t;
+#endif
   }
+#ifdef OSIM_PLANTED_MISTAKES
   if (s->mutation == M_NO_GATE_FILTER) cancel = 0;
+#endif
   if (cancel) {
     /* the new edge would come too soon after E: cancel E instead, and the
        kept edge before it (if still ahead) becomes the last kept one */
     s->cancelled[top] = 1;
     int64_t b = s->below[top];
+#ifdef OSIM_PLANTED_MISTAKES
     if (s->mutation == M_GATE_STACK_DEPTH_ONE) b = NONE;
+#endif
     if (b != NONE && s->cancelled[b] == 0) {
       s->last_seq[g] = b;
       s->last_time[g] = s->seq_time[b];
@@ -434,8 +503,10 @@ API int64_t osim_run_window(osim_t* s, int32_t w) {
   /* initial (settled) values: inputs from the stimulus, gates by zero-delay
      evaluation in net order (fanins always have lower ids) */
   for (int32_t i = 0; i < I; ++i) {
-    int64_t before = s->mutation == M_WINDOW_INIT_FROM_CYCLE0
-                         ? 0 : s->edge_ptr[(int64_t)i * s->C + c0] - s->edge_ptr[(int64_t)i * s->C];
+    int64_t before = s->edge_ptr[(int64_t)i * s->C + c0] - s->edge_ptr[(int64_t)i * s->C];
+#ifdef OSIM_PLANTED_MISTAKES
+    if (s->mutation == M_WINDOW_INIT_FROM_CYCLE0) before = 0;
+#endif
     s->netval[i] = (uint8_t)(s->init[i] ^ (before & 1));
   }
   for (int32_t g = 0; g < G; ++g) {
@@ -495,7 +566,11 @@ API int64_t osim_run_window(osim_t* s, int32_t w) {
       if (s->gate_of_pin[(int32_t)(nx->key & 0xffffffffu)] != g) break;
       cur = heap_pop(s);
     }
+#ifdef OSIM_PLANTED_MISTAKES
     if (s->mutation == M_MSI_LOWEST_PIN) istar = ilow;
+#else
+    (void)ilow;
+#endif
     if (gate_eval(s, g, t, istar, col_before)) return -1;
   }
   /* group the time-ordered log by net (stable counting sort) */
@@ -517,7 +592,10 @@ API int64_t osim_run_window(osim_t* s, int32_t w) {
     int64_t t1 = 0, prev = 0;
     for (int64_t k = s->res_ptr[n]; k < s->res_ptr[n + 1]; ++k) {
       int64_t t = s->res_times[k];
-      if (s->mutation != M_T1_UNCLIPPED && t > s->res_len) t = s->res_len;
+      if (t > s->res_len) t = s->res_len;
+#ifdef OSIM_PLANTED_MISTAKES
+      if (s->mutation == M_T1_UNCLIPPED) t = s->res_times[k];
+#endif
       if (v) t1 += t - prev;
       prev = t;
       v ^= 1;

@@ -36,9 +36,15 @@ def _pulse(case):
     return p.get("gate", 100), p.get("wire", 100)
 
 
-def _event_windows(wl, W, mutation="none", pulse=(100, 100)):
+def _features(case):
+    f = case.get("features", {})
+    return f.get("interconnect_filter", True), f.get("full_sdf", True)
+
+
+def _event_windows(wl, W, mutation="none", pulse=(100, 100), features=(True, True)):
     sim = oracle.EventSim(wl.netlist, wl.delays, wl.stim, W=W, mutation=mutation,
-                          pulse_gate=pulse[0], pulse_wire=pulse[1])
+                          pulse_gate=pulse[0], pulse_wire=pulse[1], interconnect_filter=features[0],
+                          full_sdf=features[1])
     out = []
     for w in range(sim.num_windows):
         out.append(oracle.windows_as_lists(*sim.window(w)))
@@ -47,7 +53,7 @@ def _event_windows(wl, W, mutation="none", pulse=(100, 100)):
 
 def _golden_failures(case, mutation="none"):
     wl = case_workload(case)
-    sim, wins = _event_windows(wl, case["W"], mutation, _pulse(case))
+    sim, wins = _event_windows(wl, case["W"], mutation, _pulse(case), _features(case))
     fails = []
     for e in case["expect"]:
         got = wins[e["window"]][e["net"]]
@@ -72,7 +78,10 @@ def test_hand_traced_algo1(case):
     W = case["W"]
     nwin = (wl.stim.num_cycles + W - 1) // W
     pg, pw = _pulse(case)
-    wins = [algo1.simulate_window(wl.netlist, wl.delays, wl.stim, w, W, pg, pw) for w in range(nwin)]
+    wire_filter, full_sdf = _features(case)
+    if not wire_filter:
+        pw = 0  # the interconnect test deleted: only crossing arrivals cancel
+    wins = [algo1.simulate_window(wl.netlist, wl.delays, wl.stim, w, W, pg, pw, full_sdf) for w in range(nwin)]
     for e in case["expect"]:
         init, times = wins[e["window"]][e["net"]]
         assert (init, list(times)) == (e["init"], e["times"])
@@ -321,6 +330,34 @@ def test_event_sim_matches_algorithm1_random_pulse_limits(block):
             ev = oracle.windows_as_lists(*sim.window(w))
             a1 = [(i, list(t)) for i, t in algo1.simulate_window(wl.netlist, wl.delays, wl.stim, w, W, pg, pw)]
             assert ev == a1, f"random case {s} window {w} limits {pg}/{pw}"
+
+
+@pytest.mark.parametrize("wire_filter,full_sdf", [(False, True), (True, False), (False, False)])
+def test_event_sim_matches_algorithm1_reduced_features(wire_filter, full_sdf):
+    """The paper's reduced-feature variants (Section 5, Table "features"):
+    no interconnect filter, averaged (partial-SDF) arc delays, and both."""
+    for s in range(9000, 9300):
+        wl = gen.random_small(s)
+        W = 1 + s % 2
+        sim = oracle.EventSim(wl.netlist, wl.delays, wl.stim, W=W, interconnect_filter=wire_filter,
+                              full_sdf=full_sdf)
+        for w in range(sim.num_windows):
+            ev = oracle.windows_as_lists(*sim.window(w))
+            a1 = [(i, list(t)) for i, t in algo1.simulate_window(
+                wl.netlist, wl.delays, wl.stim, w, W, 100, 100 if wire_filter else 0, full_sdf)]
+            assert ev == a1, f"random case {s} window {w}"
+    # settled values and invariants hold in both variants too
+    wl = gen.make_workload("tiny", seed=13, num_cycles=40)
+    sim = oracle.EventSim(wl.netlist, wl.delays, wl.stim, W=1, interconnect_filter=wire_filter,
+                          full_sdf=full_sdf)
+    t0, t1, tc = sim.saif()
+    assert np.all(t0 + t1 == 40 * wl.stim.cycle_ps) and np.all(t0 >= 0) and np.all(t1 >= 0)
+    for w in (0, 17, 39):
+        init, ptr, times = sim.window(w)
+        final = init ^ (np.diff(ptr) & 1).astype(np.uint8)
+        assert np.array_equal(final, _zero_delay(wl.netlist, _final_input_values(wl.stim, w, 1)))
+        for n in range(sim.N):
+            assert np.all(np.diff(times[ptr[n]:ptr[n + 1]]) > 0)
 
 
 def test_event_sim_matches_algorithm1_recipes():
