@@ -19,6 +19,7 @@
 #include "gatspi.h"
 #include "host_common.h"
 #include "kernels.cuh"
+#include "digest.cuh"
 
 using namespace gatspi_dev;
 
@@ -53,6 +54,7 @@ struct EJob {
   int32_t* d_gate_delta = nullptr;
   unsigned long long* d_t1 = nullptr;
   unsigned long long* d_tc = nullptr;
+  unsigned long long* d_digest = nullptr;  // [N] waveform digests (engine option)
   int32_t parts_total = 0, parts_done = 0;
   int state = GATSPI_JOB_QUEUED;
   std::string err;
@@ -243,6 +245,7 @@ void free_job_device(EJob& j, cudaStream_t s) {
   }
   dfree_async(j.d_edge_ptr, s); dfree_async(j.d_edge_time, s); dfree_async(j.d_init_in, s);
   dfree_async(j.d_gate_delta, s); dfree_async(j.d_t1, s); dfree_async(j.d_tc, s);
+  dfree_async(j.d_digest, s);
   if (j.done_ev) cudaEventDestroy(j.done_ev);
   j.done_ev = nullptr;
   if (j.ready_ev) cudaEventDestroy(j.ready_ev);
@@ -366,6 +369,19 @@ int retire(gatspi_engine* eng, bool wait_one) {
       const int32_t N = nl.r.N;
       saif_add_kernel<<<(N + 255) / 256, 256, 0, eng->stream>>>(N, p.t1, p.tc, j.d_t1, j.d_tc);
       eng->stats.kernel_launches++;
+      if (j.d_digest) {  // the part's waveforms, read before its memory is freed below
+        DigestParams q{};
+        q.rmeta = p.rmeta; q.tinfo = p.tinfo; q.rstart = p.rstart;
+        q.net_level = nl.d_net_level; q.lvl_base = p.lvl_base; q.times = p.times;
+        q.capacity = p.cap; q.out = j.d_digest; q.status = p.status;
+        q.N = N; q.NW = p.nw; q.w0 = p.w0;
+        q.TW = p.T > 0 ? p.TW : 128;
+        q.T = (p.nw + q.TW - 1) / q.TW;
+        const long long warps = (long long)q.N * q.T;
+        digest_kernel<<<(unsigned)((warps + 7) / 8), 256, 0, eng->stream>>>(q);
+        ECK(cudaGetLastError());
+        eng->stats.kernel_launches++;
+      }
       const double obs = (double)res.edges / ((double)N * p.nw);
       nl.edges_per_item = std::max(nl.edges_per_item * 0.98, obs * 1.1);
       j.parts_done++;
@@ -398,7 +414,7 @@ int gatspi_engine_create(gatspi_engine** out, int device, size_t arena_bytes, co
     }
     gatspi_engine_opts o{};
     if (opts) o = *opts;
-    if (o.reserved || o.step_items < 0) return GATSPI_EINVAL;
+    if (o.digest < 0 || o.digest > 1 || o.step_items < 0) return GATSPI_EINVAL;
     const int nt = o.tile_items ? o.tile_items : 256;
     const int ipt = o.items_per_thread ? o.items_per_thread : 4;
     if ((nt != 128 && nt != 256 && nt != 512) || (ipt != 1 && ipt != 2 && ipt != 4 && ipt != 8) ||
@@ -557,6 +573,10 @@ int gatspi_engine_submit(gatspi_engine* eng, int32_t netlist_id, int32_t num_cyc
     if ((rc = eupload_async<unsigned long long>(eng, j->d_tc, nullptr, nl.r.N))) return undo(rc);
     ECK(cudaMemsetAsync(j->d_t1, 0, sizeof(unsigned long long) * nl.r.N, eng->upload));
     ECK(cudaMemsetAsync(j->d_tc, 0, sizeof(unsigned long long) * nl.r.N, eng->upload));
+    if (eng->opts.digest) {
+      if ((rc = eupload_async<unsigned long long>(eng, j->d_digest, nullptr, nl.r.N))) return undo(rc);
+      ECK(cudaMemsetAsync(j->d_digest, 0, sizeof(unsigned long long) * nl.r.N, eng->upload));
+    }
     ECK(cudaEventCreateWithFlags(&j->ready_ev, cudaEventDisableTiming));
     ECK(cudaEventRecord(j->ready_ev, eng->upload));
     // cut into parts of at most part_items (gate, window) items and a level
@@ -853,6 +873,27 @@ int gatspi_engine_poll(gatspi_engine* eng, int64_t job_id, int32_t* state, int64
       }
     }
     if (j.state == GATSPI_JOB_FAILED) return efail(eng, GATSPI_OK, j.err);
+    return GATSPI_OK;
+  });
+}
+
+int gatspi_engine_digest(gatspi_engine* eng, int64_t job_id, uint64_t* per_net) {
+  return guarded(eng, [&]() -> int {
+    if (!eng || !per_net) return GATSPI_EINVAL;
+    auto it = eng->jobs.find(job_id);
+    if (it == eng->jobs.end()) return efail(eng, GATSPI_EINVAL, "unknown job id");
+    EJob& j = *it->second;
+    ECK(cudaSetDevice(eng->device));
+    if (j.state != GATSPI_JOB_FAILED && j.done_recorded && cudaEventQuery(j.done_ev) == cudaSuccess)
+      j.state = GATSPI_JOB_DONE;
+    cudaGetLastError();
+    if (j.state != GATSPI_JOB_DONE) return efail(eng, GATSPI_ESTATE, "job not done");
+    if (!j.d_digest) return efail(eng, GATSPI_ESTATE, "the engine was created without digests");
+    const ENetlist& nl = *eng->nets[j.net];
+    const int32_t N = nl.r.N;
+    std::vector<unsigned long long> d(N);
+    ECK(cudaMemcpy(d.data(), j.d_digest, sizeof(unsigned long long) * N, cudaMemcpyDeviceToHost));
+    for (int32_t e = 0; e < N; ++e) per_net[e] = (uint64_t)d[nl.r.net_int[e]];
     return GATSPI_OK;
   });
 }

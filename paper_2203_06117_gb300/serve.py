@@ -35,6 +35,7 @@ class Request:
     edit_gate: np.ndarray | None = None
     edit_delta: np.ndarray | None = None
     result: tuple | None = None
+    digest: np.ndarray | None = None  # per-net waveform digests, when asked for
     done: float = field(default=float("nan"))
 
     @property
@@ -71,6 +72,8 @@ def run_batched(netlists, reqs, keep_results=True, **engine_opts):
             if state != JOB_DONE:
                 raise RuntimeError(f"job {j} ended in state {state}")
             r.result = saif
+            if engine_opts.get("digest"):
+                r.digest = eng.digest(j, ids[r.netlist])
             r.done = time.perf_counter() - t0
         dt = time.perf_counter() - t0
         return dt, eng.stats()
@@ -114,8 +117,11 @@ def _dummy_stim(wl):
 
 
 def run_served(netlists, reqs, keep_results=True, **engine_opts):
-    """Open-loop stream with continuous batching.  Returns (makespan, stats)."""
+    """Open-loop stream with continuous batching.  Returns (makespan, stats).
+    With ``digest=1`` among the engine options each request also gets its
+    per-net waveform digests (read before the request is released)."""
     reqs = sorted(reqs, key=lambda r: r.arrival)
+    want_digest = bool(engine_opts.get("digest"))
     with Engine(**engine_opts) as eng:
         ids = [eng.add_netlist(w.netlist, w.delays) for w in netlists]
         inflight = {}
@@ -139,6 +145,8 @@ def run_served(netlists, reqs, keep_results=True, **engine_opts):
                 if state == JOB_DONE:
                     r.done = time.perf_counter() - t0
                     r.result = saif
+                    if want_digest:
+                        r.digest = eng.digest(j, ids[r.netlist])
                     eng.release(j)
                     del inflight[j]
                 elif state == JOB_FAILED:

@@ -74,6 +74,42 @@ def test_batched_jobs_match_oracle():
             assert_saif(saif, oracle_saif(nets[n].netlist, dl, st, W), f"job {jid}")
 
 
+def test_engine_digests_match_oracle():
+    """Per-job waveform digests (every waveform of every window) equal the
+    oracle's, for jobs split into several parts, with and without edits."""
+    from oracle import digest as odig
+    nets = small_netlists()
+    rng = np.random.Generator(np.random.PCG64(4))
+    with gs.Engine(part_items=25_000, digest=1) as eng:
+        ids = [eng.add_netlist(w.netlist, w.delays) for w in nets]
+        jobs = []
+        for k in range(10):
+            n = k % len(nets)
+            st = job_stimulus(nets[n], 4000 + k, int(rng.integers(20, 120)))
+            W = 1 + k % 3
+            edit = None
+            if k % 2:
+                G = nets[n].netlist.num_gates
+                gates = rng.choice(G, size=max(1, G // 50), replace=False)
+                edit = (gates, rng.choice([-1, 1], size=gates.size) * rng.integers(10, 51, size=gates.size))
+            jobs.append((eng.submit(ids[n], st, W, *(edit or (None, None))), n, st, W, edit))
+        eng.drain()
+        assert eng.stats()["parts_done"] > 10            # several jobs span more than one part
+        for jid, n, st, W, edit in jobs:
+            dl = nets[n].delays if edit is None else edited_delays(nets[n].netlist, nets[n].delays, *edit)
+            ref = oracle.EventSim(nets[n].netlist, dl, st, W=W)
+            got = eng.digest(jid, ids[n])
+            want = odig.digest(ref, range(ref.num_windows))
+            assert np.array_equal(got, want), f"job {jid}: {np.count_nonzero(got != want)} nets differ"
+    with gs.Engine() as eng:                             # no digests asked for
+        nid = eng.add_netlist(nets[0].netlist, nets[0].delays)
+        j = eng.submit(nid, job_stimulus(nets[0], 9, 10))
+        eng.drain()
+        with pytest.raises(gs.GatspiError) as e:
+            eng.digest(j, nid)
+        assert e.value.code == gs.ESTATE
+
+
 def test_same_alone_and_in_the_mix():
     """A job's SAIF does not depend on what else runs with it, and equals the
     plain single-job path."""
