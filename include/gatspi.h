@@ -104,8 +104,27 @@ typedef struct gatspi_opts {
                             of consecutive segments add up to those of the
                             whole run, and a run can resume at any window */
   int32_t num_windows;   /* 0 = through the last window */
-  int32_t reserved;      /* must be 0 */
+  int32_t features;      /* 0 = Algorithm 1 with every feature.  The paper's
+                            variants without some features, to measure their
+                            cost (Section 5, Table "features"), as a mask:
+                            GATSPI_NO_INTERCONNECT_FILTER deletes the
+                            interconnect inertial test (two consecutive edges
+                            of a pin whose delayed arrivals would cross or
+                            coincide still cancel as a pair, which keeps
+                            every pin's arrivals in time order);
+                            GATSPI_PARTIAL_SDF gives every arc one delay per
+                            output edge, the mean of its table over all COND
+                            columns and both input edges, rounded to the
+                            nearest ps (halves up), computed from the delays
+                            loaded (a delay edit then shifts it).  Needs pulse
+                            limits of 100 / 100; the launch shape is 256
+                            threads x 4 windows (or x 1); no cone
+                            re-simulation (gatspi_resimulate_edit runs the
+                            whole simulation again) */
 } gatspi_opts;
+
+#define GATSPI_NO_INTERCONNECT_FILTER 1
+#define GATSPI_PARTIAL_SDF 2
 
 /* Figures of the last gatspi_simulate call. */
 typedef struct gatspi_stats {
@@ -370,7 +389,8 @@ typedef struct gatspi_engine_opts {
   int64_t part_items;  /* max (gate, window) items of one part; 0 = 2^30 */
   int32_t items_per_thread; /* 1, 2, 4, 8 (at most 4 with 512 threads);
                                0 = 4 */
-  int32_t reserved;    /* must be 0 */
+  int32_t digest;      /* 1: every job also reduces its waveforms to per-net
+                          digests (gatspi_engine_digest); 0 = off */
   int64_t step_items;  /* admission stops while the parts in flight hold
                           this many (gate, window) items per level on
                           average: enough to fill the GPU in one launch,
@@ -442,6 +462,14 @@ int gatspi_engine_drain(gatspi_engine* eng);
  * caller's net numbering; any may be NULL).  Errors: EINVAL (unknown id). */
 int gatspi_engine_poll(gatspi_engine* eng, int64_t job_id, int32_t* state, int64_t* t0,
                        int64_t* t1, int64_t* tc);
+
+/* Per-net waveform digests of a finished job (uint64 [I+G], caller's net
+ * numbering), with the definition of gatspi_digest over all of the job's
+ * windows (window indices are the job's own).  The check of bit-exactness
+ * at scale for batched and served jobs (Section 4 compares SAIF and
+ * spot-checks waveforms).  Needs an engine created with digest = 1.
+ * Errors: EINVAL (unknown id, NULL), ESTATE (job not done, or no digests). */
+int gatspi_engine_digest(gatspi_engine* eng, int64_t job_id, uint64_t* per_net);
 
 /* Forget a finished job and free its device memory.  Errors: EINVAL,
  * ESTATE (job not finished). */

@@ -46,7 +46,7 @@ EXPORTS = ["gatspi_create", "gatspi_destroy", "gatspi_last_error", "gatspi_load_
            "gatspi_engine_create", "gatspi_engine_destroy", "gatspi_engine_last_error",
            "gatspi_engine_add_netlist", "gatspi_engine_submit", "gatspi_engine_step",
            "gatspi_engine_drain", "gatspi_engine_poll", "gatspi_engine_release",
-           "gatspi_engine_get_stats", "gatspi_propagate_level_noalloc", "gatspi_resimulate_edit",
+           "gatspi_engine_get_stats", "gatspi_engine_digest", "gatspi_propagate_level_noalloc", "gatspi_resimulate_edit",
            "gatspi_set_stimulus_events", "gatspi_vcd_read", "gatspi_saif_write"]
 
 JOB_QUEUED, JOB_RUNNING, JOB_DONE, JOB_FAILED = 0, 1, 2, 3
@@ -86,13 +86,13 @@ class gatspi_opts(ctypes.Structure):
                 ("items_per_thread", ctypes.c_int32), ("digest", ctypes.c_int32),
                 ("pulse_limits", ctypes.c_int32), ("gate_pulse_percent", ctypes.c_int32),
                 ("wire_pulse_percent", ctypes.c_int32), ("first_window", ctypes.c_int32),
-                ("num_windows", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("num_windows", ctypes.c_int32), ("features", ctypes.c_int32)]
 
 
 class gatspi_engine_opts(ctypes.Structure):
     _fields_ = [("tile_items", ctypes.c_int32), ("max_active", ctypes.c_int32),
                 ("part_items", ctypes.c_int64), ("items_per_thread", ctypes.c_int32),
-                ("reserved", ctypes.c_int32), ("step_items", ctypes.c_int64)]
+                ("digest", ctypes.c_int32), ("step_items", ctypes.c_int64)]
 
 
 class gatspi_engine_stats(ctypes.Structure):
@@ -185,6 +185,7 @@ def lib():
         L.gatspi_engine_drain.argtypes = [vp]
         L.gatspi_engine_poll.argtypes = [vp, i64, ctypes.POINTER(ctypes.c_int32), vp, vp, vp]
         L.gatspi_engine_release.argtypes = [vp, i64]
+        L.gatspi_engine_digest.argtypes = [vp, i64, vp]
         L.gatspi_engine_get_stats.argtypes = [vp, ctypes.POINTER(gatspi_engine_stats)]
         L.gatspi_propagate_level_noalloc.argtypes = [ctypes.POINTER(gatspi_level_args), vp]
         for name in EXPORTS:
@@ -306,16 +307,22 @@ def gatspi_set_stimulus(ctx, num_cycles, cycle_ps, init, edge_ptr, edge_time) ->
                                           _ptr(et)))
 
 
+#: features masks of gatspi_opts (the paper's variants without them)
+NO_INTERCONNECT_FILTER, PARTIAL_SDF = 1, 2
+
+
 def gatspi_simulate(ctx, window_cycles=0, batch_windows=0, tile_items=0, time_kernels=0,
-                    items_per_thread=0, digest=0, pulse=None, first_window=0, num_windows=0) -> None:
+                    items_per_thread=0, digest=0, pulse=None, first_window=0, num_windows=0,
+                    features=0) -> None:
     """``pulse``: None for Algorithm 1 as printed, else (gate percent, wire
     percent), the PATHPULSEPERCENT limits of the two inertial tests.
     ``first_window`` / ``num_windows``: a segment of the windows (0 = to the
-    end); segments' SAIF and digests add up to the whole run's."""
+    end); segments' SAIF and digests add up to the whole run's.
+    ``features``: a mask of NO_INTERCONNECT_FILTER and PARTIAL_SDF."""
     pg, pw = pulse if pulse is not None else (100, 100)
     o = gatspi_opts(int(window_cycles), int(batch_windows), int(tile_items), int(time_kernels),
                     int(items_per_thread), int(digest), 1 if pulse is not None else 0, int(pg), int(pw),
-                    int(first_window), int(num_windows))
+                    int(first_window), int(num_windows), int(features))
     _check(ctx, lib().gatspi_simulate(ctx, ctypes.byref(o)))
 
 
@@ -410,10 +417,10 @@ def _echeck(eng, rc):
 
 
 def gatspi_engine_create(device=0, arena_bytes=0, tile_items=0, max_active=0, part_items=0,
-                         items_per_thread=0, step_items=0):
+                         items_per_thread=0, step_items=0, digest=0):
     h = ctypes.c_void_p()
-    o = gatspi_engine_opts(int(tile_items), int(max_active), int(part_items), int(items_per_thread), 0,
-                           int(step_items))
+    o = gatspi_engine_opts(int(tile_items), int(max_active), int(part_items), int(items_per_thread),
+                           int(digest), int(step_items))
     rc = lib().gatspi_engine_create(ctypes.byref(h), int(device), int(arena_bytes), ctypes.byref(o))
     if rc != OK:
         raise GatspiError(rc, f"cannot create an engine on device {device}")
@@ -474,6 +481,13 @@ def gatspi_engine_poll(eng, job_id, num_nets=None):
     return st.value, ((t0, t1, tc) if st.value == JOB_DONE else None)
 
 
+def gatspi_engine_digest(eng, job_id, num_nets) -> np.ndarray:
+    """Per-net waveform digests (uint64 [num_nets]) of a finished job."""
+    out = np.empty(num_nets, np.uint64)
+    _echeck(eng, lib().gatspi_engine_digest(eng, int(job_id), _ptr(out)))
+    return out
+
+
 def gatspi_engine_release(eng, job_id) -> None:
     _echeck(eng, lib().gatspi_engine_release(eng, int(job_id)))
 
@@ -507,6 +521,9 @@ class Engine:
 
     def poll(self, job_id, netlist_id=None):
         return gatspi_engine_poll(self.h, job_id, None if netlist_id is None else self.nets[netlist_id])
+
+    def digest(self, job_id, netlist_id):
+        return gatspi_engine_digest(self.h, job_id, self.nets[netlist_id])
 
     def release(self, job_id):
         gatspi_engine_release(self.h, job_id)

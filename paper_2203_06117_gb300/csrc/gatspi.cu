@@ -64,6 +64,7 @@ struct gatspi_ctx {
   int32_t* d_gate_desc = nullptr;
   uint16_t* d_lut = nullptr;
   int32_t* d_gate_delay = nullptr;
+  int32_t* d_gate_delay_avg = nullptr;  // partial-SDF table (GATSPI_PARTIAL_SDF)
   int32_t* d_wire_delay = nullptr;
   int32_t* d_gate_delta = nullptr;  // delay edit per internal gate, or null
   int32_t max_edit = 0;
@@ -97,6 +98,7 @@ struct gatspi_ctx {
   int64_t generation = 0;      // bumped by every load/edit/stimulus call
   int eager_nt = 0, eager_ipt = 0;  // a launch shape already run eagerly
   bool eager_pp = false;             // ... and whether with pulse limits
+  int eager_feat = 0;                // ... and the features left out
   long long* d_in_prefix = nullptr;
   int64_t total_time = 0;
 
@@ -195,7 +197,7 @@ void free_netlist(gatspi_ctx* c) {
   dfree(c->d_cone);
   dfree(c->d_fanin_ptr); dfree(c->d_fanin_net); dfree(c->d_net_level); dfree(c->d_lut);
   dfree(c->d_gate_desc);
-  dfree(c->d_gate_delay); dfree(c->d_wire_delay); dfree(c->d_t1); dfree(c->d_tc); dfree(c->d_digest);
+  dfree(c->d_gate_delay); dfree(c->d_gate_delay_avg); dfree(c->d_wire_delay); dfree(c->d_t1); dfree(c->d_tc); dfree(c->d_digest);
   c->have_digest = false;
   dfree(c->d_in_prefix);
   dfree(c->d_bounds);
@@ -435,6 +437,8 @@ int gatspi_load_delays(gatspi_ctx* ctx, const int32_t* gate_delay, const int32_t
     int rc;
     if ((rc = upload(ctx, ctx->d_gate_delay, gd.data(), gd.size()))) return rc;
     if ((rc = upload(ctx, ctx->d_wire_delay, wd.data(), wd.size()))) return rc;
+    const std::vector<int32_t> avg = gatspi_host::averaged_delays(ctx->fanin_ptr, ctx->G, gd);
+    if ((rc = upload(ctx, ctx->d_gate_delay_avg, avg.data(), avg.size()))) return rc;
     ctx->max_gate_delay = mg;
     ctx->max_wire_delay = mw;
     dfree(ctx->d_gate_delta);
@@ -592,10 +596,12 @@ int gatspi_set_stimulus_events(gatspi_ctx* ctx, int32_t num_cycles, int32_t cycl
 namespace {
 
 // The kernels' view of the loaded job and the carved batch.
-JobView job_view(const gatspi_ctx* ctx, int32_t nw, int32_t w0, int32_t W, int32_t pulse_g, int32_t pulse_w) {
+JobView job_view(const gatspi_ctx* ctx, int32_t nw, int32_t w0, int32_t W, int32_t pulse_g, int32_t pulse_w,
+                 int32_t features = 0) {
   JobView job{};
   job.fanin_ptr = ctx->d_fanin_ptr; job.fanin_net = ctx->d_fanin_net; job.lut = ctx->d_lut;
-  job.gate_delay = ctx->d_gate_delay; job.wire_delay = ctx->d_wire_delay;
+  job.gate_delay = (features & GATSPI_PARTIAL_SDF) ? ctx->d_gate_delay_avg : ctx->d_gate_delay;
+  job.wire_delay = ctx->d_wire_delay;
   job.net_level = ctx->d_net_level; job.gate_delta = ctx->d_gate_delta;
   job.gdesc = (const int4*)ctx->d_gate_desc;
   job.rstart = ctx->d_rstart; job.tinfo = ctx->d_tinfo; job.T = ctx->batch_T; job.rmeta = ctx->d_rmeta;
@@ -614,7 +620,9 @@ int simulate_impl(gatspi_ctx* ctx, const gatspi_opts* opts) {
   CK(cudaSetDevice(ctx->device));
   gatspi_opts o{};
   if (opts) o = *opts;
-  if (o.reserved) return fail(ctx, GATSPI_EINVAL, "reserved option fields must be 0");
+  const int32_t feat = o.features;
+  if (feat < 0 || feat > (GATSPI_NO_INTERCONNECT_FILTER | GATSPI_PARTIAL_SDF))
+    return fail(ctx, GATSPI_EINVAL, "features must be a mask of GATSPI_NO_INTERCONNECT_FILTER and GATSPI_PARTIAL_SDF");
   if (o.digest < 0 || o.digest > 1) return fail(ctx, GATSPI_EINVAL, "digest must be 0 or 1");
   if (o.pulse_limits < 0 || o.pulse_limits > 1) return fail(ctx, GATSPI_EINVAL, "pulse_limits must be 0 or 1");
   const int32_t pulse_g = o.pulse_limits ? o.gate_pulse_percent : 100;
@@ -634,6 +642,9 @@ int simulate_impl(gatspi_ctx* ctx, const gatspi_opts* opts) {
   if (pp && !pulse_variant_compiled(nt, ipt))
     return fail(ctx, GATSPI_EINVAL, "with pulse limits the launch shape must be 256 x 1, 256 x 2, 256 x 4 "
                                     "or 128 x 8 (threads x items_per_thread)");
+  if (feat && pp) return fail(ctx, GATSPI_EINVAL, "features need pulse limits of 100 / 100");
+  if (feat && !(nt == 256 && (ipt == 1 || ipt == 4)))
+    return fail(ctx, GATSPI_EINVAL, "without features the launch shape must be 256 x 4 or 256 x 1");
   const int tile = tile_items_of(ipt);  // items per warp tile
   if (o.batch_windows < 0) return fail(ctx, GATSPI_EINVAL, "batch_windows must be >= 0");
   // every time stays below 2^31: window length plus the longest path
@@ -750,7 +761,7 @@ int simulate_impl(gatspi_ctx* ctx, const gatspi_opts* opts) {
         if ((e = cudaGetLastError())) return e;
         if (o.time_kernels && (e = rec(ctx->ev[1]))) return e;
       }
-      const JobView job = job_view(ctx, nw, w0, W, pulse_g, pulse_w);
+      const JobView job = job_view(ctx, nw, w0, W, pulse_g, pulse_w, feat);
       for (int32_t l = 1; l <= ctx->D; ++l) {
         PropParams p{};
         p.job = job;
@@ -764,6 +775,18 @@ int simulate_impl(gatspi_ctx* ctx, const gatspi_opts* opts) {
         if (pp) {
           SingleLaunchMode<kModePulse> go{&p, ctx->stream};
           launch_variant_pp(nt, ipt, go);
+          e = go.err;
+        } else if (feat == GATSPI_NO_INTERCONNECT_FILTER) {
+          SingleLaunchMode<kModeNoWireFilter> go{&p, ctx->stream};
+          launch_variant_features(ipt, go);
+          e = go.err;
+        } else if (feat == GATSPI_PARTIAL_SDF) {
+          SingleLaunchMode<kModeAvgSdf> go{&p, ctx->stream};
+          launch_variant_features(ipt, go);
+          e = go.err;
+        } else if (feat) {
+          SingleLaunchMode<kModeNoWireAvgSdf> go{&p, ctx->stream};
+          launch_variant_features(ipt, go);
           e = go.err;
         } else {
           SingleLaunch go{&p, ctx->stream};
@@ -802,9 +825,10 @@ int simulate_impl(gatspi_ctx* ctx, const gatspi_opts* opts) {
     const std::vector<long long> key = {
         ctx->generation, (long long)(uintptr_t)ctx->d_arena, (long long)ctx->arena_bytes, ctx->times_cap,
         nw, w0, W, nt, ipt, o.digest, o.time_kernels, record_first ? 1 : 0, l0, ctx->batch_T,
-        (long long)(uintptr_t)ctx->d_gate_delta, pulse_g, pulse_w};
+        (long long)(uintptr_t)ctx->d_gate_delta, pulse_g, pulse_w, feat};
     bool done = false;
-    if (ctx->eager_nt == nt && ctx->eager_ipt == ipt && ctx->eager_pp == pp) {  // the variant's attributes are set
+    if (ctx->eager_nt == nt && ctx->eager_ipt == ipt && ctx->eager_pp == pp &&
+        ctx->eager_feat == feat) {  // the variant's attributes are set
       if (!(ctx->gexec && ctx->gkey == key)) {
         if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
         ctx->gexec = nullptr;
@@ -835,6 +859,7 @@ int simulate_impl(gatspi_ctx* ctx, const gatspi_opts* opts) {
       ctx->eager_nt = nt;
       ctx->eager_ipt = ipt;
       ctx->eager_pp = pp;
+      ctx->eager_feat = feat;
     }
     if (record_first) first_recorded = true;
     st.kernel_launches += 1 + ctx->D + (o.digest ? 1 : 0);
@@ -973,7 +998,7 @@ int gatspi_simulate(gatspi_ctx* ctx, const gatspi_opts* opts) {
     gatspi_opts o{};
     if (opts) o = *opts;
     const bool pp = o.pulse_limits == 1 && (o.gate_pulse_percent != 100 || o.wire_pulse_percent != 100);
-    if (o.tile_items == 0 && o.items_per_thread == 0 && !pp) {
+    if (o.tile_items == 0 && o.items_per_thread == 0 && !pp && !o.features) {
       if (!ctx->tuned_nt) {
         const int rc = autotune(ctx, o);
         if (rc) return rc;
@@ -1039,7 +1064,8 @@ int gatspi_resimulate_edit(gatspi_ctx* ctx, int32_t n_edits, const int32_t* edit
       if (info) *info = r;
       return GATSPI_OK;
     }
-    if (!resident) return full();
+    // the cone launches carry every feature: without some, run it all again
+    if (!resident || o.features) return full();
     // the fanout cone of the changed gates, level by level (gates are sorted
     // by level, so one pass in gate order reaches every cone gate after its
     // fanins)

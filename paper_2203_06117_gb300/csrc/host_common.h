@@ -153,6 +153,34 @@ inline std::string prepare_delays(const Prepared& r, const int32_t* gate_delay, 
   return "";
 }
 
+// The partial-SDF table (the paper's variant without full SDF, Section 5,
+// Table "features"): every entry of an arc -- its 2 input edges x 2^(n-1)
+// COND columns for one output edge -- replaced by their mean, rounded to the
+// nearest ps (halves up); unused columns keep the value too.  `gd` is the
+// internal-order table [P][2][2][8].
+inline std::vector<int32_t> averaged_delays(const std::vector<int32_t>& fanin_ptr, int32_t G,
+                                            const std::vector<int32_t>& gd) {
+  std::vector<int32_t> out(gd.size(), 1);
+  for (int32_t j = 0; j < G; ++j) {
+    const int32_t k = fanin_ptr[j + 1] - fanin_ptr[j];
+    const int32_t ncol = 1 << (k - 1);
+    for (int32_t pi = fanin_ptr[j]; pi < fanin_ptr[j + 1]; ++pi) {
+      const int32_t* d = &gd[(size_t)pi * 32];
+      int32_t* a = &out[(size_t)pi * 32];
+      for (int oe = 0; oe < 2; ++oe) {
+        int64_t sum = 0;
+        for (int ie = 0; ie < 2; ++ie)
+          for (int32_t c = 0; c < ncol; ++c) sum += d[(2 * ie + oe) * 8 + c];
+        const int64_t cnt = 2 * (int64_t)ncol;
+        const int32_t avg = (int32_t)((sum + cnt / 2) / cnt);
+        for (int ie = 0; ie < 2; ++ie)
+          for (int c = 0; c < 8; ++c) a[(2 * ie + oe) * 8 + c] = avg;
+      }
+    }
+  }
+  return out;
+}
+
 // Checks one range of (input, cycle) slots; returns the first bad slot and
 // why (0 = fine) in *bad / *kind.
 inline void validate_slots(int64_t k0, int64_t k1, int32_t L, const int64_t* edge_ptr, const int32_t* edge_time,

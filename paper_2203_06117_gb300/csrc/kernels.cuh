@@ -139,6 +139,18 @@ __device__ __forceinline__ int32_t window_len(int32_t wg, int32_t W, int32_t C, 
   return (c1 - c0) * L;
 }
 
+// Features of Algorithm 1 a kernel can be compiled without, as the paper
+// does to measure their cost (Section 5, Table "features"):
+//   kNoWireFilter -- the interconnect inertial test deleted: every edge
+//     arrives after its delay, except that two consecutive edges of a pin
+//     whose arrivals would cross or coincide cancel as a pair (Algorithm 1
+//     assumes each pin's arrivals in time order);
+//   kAvgSdf -- partial SDF: each arc keeps one delay per output edge, the
+//     mean over its COND columns and input edges, which the host stores in
+//     every entry of the arc's table; the kernel reads the entry of row
+//     outEdge, column 0, without the input-edge and COND index.
+constexpr int kNoWireFilter = 1, kAvgSdf = 2;
+
 // One fanin pin of one (gate, window) item.
 struct Pin {
   const int32_t* t;  // edge times of the driving net in this window
@@ -156,12 +168,17 @@ struct Pin {
 // The edge times may sit in shared memory (staged) or in global memory, so
 // they are read with generic loads (a global-only load of a shared address
 // faults).
+template <int F = 0>
 __device__ __forceinline__ void pin_advance(Pin& q) {
   int32_t j = q.j, a = kInf;
   while (j < q.n) {
     const int32_t t = q.t[j];
-    const int32_t d = (((q.v0 ^ (uint32_t)j) & 1u) == 0u) ? q.dr : q.df;
-    if (j + 1 < q.n && q.t[j + 1] - t < d) {
+    const bool rise = ((q.v0 ^ (uint32_t)j) & 1u) == 0u;
+    const int32_t d = rise ? q.dr : q.df;
+    bool drop;
+    if constexpr (F & kNoWireFilter) drop = j + 1 < q.n && q.t[j + 1] + (rise ? q.df : q.dr) <= t + d;
+    else drop = j + 1 < q.n && q.t[j + 1] - t < d;
+    if (drop) {
       j += 2;
       continue;
     }
@@ -181,7 +198,7 @@ __device__ __forceinline__ void pin_advance(Pin& q) {
 // edge has been cancelled the kept edge before it is already in the past, so
 // no deeper history is needed.  Edges are handed to `sink` as they become
 // final; T1 (time at 1 inside [0, len)) is integrated on the way.
-template <int K, class Sink>
+template <int K, int F = 0, class Sink>
 __device__ __forceinline__ void run_gate(Pin (&pin)[K], uint32_t lut,
                                          const int32_t* __restrict__ gd, int32_t edit,
                                          int32_t len, Sink& sink, int32_t& count, int32_t& t1,
@@ -192,7 +209,7 @@ __device__ __forceinline__ void run_gate(Pin (&pin)[K], uint32_t lut,
   uint32_t y = (lut >> col) & 1u;
   y0 = y;
 #pragma unroll
-  for (int i = 0; i < K; ++i) pin_advance(pin[i]);
+  for (int i = 0; i < K; ++i) pin_advance<F>(pin[i]);
   bool pend_on = false;
   int32_t pend = 0, nflush = 0, prev = 0, acc = 0;
   uint32_t cv = y;
@@ -214,7 +231,7 @@ __device__ __forceinline__ void run_gate(Pin (&pin)[K], uint32_t lut,
       if (pin[i].a == t) {  // every pin arriving now switches (MSI)
         col ^= 1u << i;
         istar = i;
-        pin_advance(pin[i]);
+        pin_advance<F>(pin[i]);
       }
     }
     const uint32_t yn = (lut >> col) & 1u;
@@ -223,9 +240,15 @@ __device__ __forceinline__ void run_gate(Pin (&pin)[K], uint32_t lut,
         pend_on = false;  // gate inertial filter: cancel the last kept edge
       } else {
         if (pend_on) flush(pend);
-        const uint32_t side = (col & ((1u << istar) - 1u)) | ((col >> (istar + 1)) << istar);
-        const uint32_t ie = (col >> istar) & 1u;
-        pend = t + max(1, gd[istar * 32 + (int)(ie * 16u + yn * 8u + side)] + edit);
+        int32_t dg;
+        if constexpr (F & kAvgSdf) {
+          dg = gd[istar * 32 + (int)(yn * 8u)];
+        } else {
+          const uint32_t side = (col & ((1u << istar) - 1u)) | ((col >> (istar + 1)) << istar);
+          const uint32_t ie = (col >> istar) & 1u;
+          dg = gd[istar * 32 + (int)(ie * 16u + yn * 8u + side)];
+        }
+        pend = t + max(1, dg + edit);
         pend_on = true;
       }
       y = yn;
@@ -403,7 +426,7 @@ __device__ __forceinline__ void load_gate(const JobView& J, int32_t g, GateCtx<K
 
 // Windows w .. w+run-1 of gate g for one lane: counts go to cnt[0..run),
 // edges to the lane's staging column, start values to bits m0.. of y0s.
-template <int K, int CAP>
+template <int K, int CAP, int F>
 __device__ __forceinline__ void simulate_run_k(const JobView& J, int32_t g, int32_t w, int32_t run,
                                                int32_t* cnt, int32_t* col, int32_t& total,
                                                uint32_t& y0s, int m0, long long& t1_acc) {
@@ -421,7 +444,7 @@ __device__ __forceinline__ void simulate_run_k(const JobView& J, int32_t g, int3
     WarpSink<CAP> sink{col, total};
     int32_t n = 0, t1 = 0;
     uint32_t y0 = 0;
-    run_gate<K>(pin, c.lut, c.gd, c.edit, window_len(J.w0 + w + j, J.W, J.C, J.L), sink, n, t1, y0);
+    run_gate<K, F>(pin, c.lut, c.gd, c.edit, window_len(J.w0 + w + j, J.W, J.C, J.L), sink, n, t1, y0);
     cnt[j] = n;
     total += n;
     y0s |= y0 << (m0 + j);
@@ -429,21 +452,21 @@ __device__ __forceinline__ void simulate_run_k(const JobView& J, int32_t g, int3
   }
 }
 
-template <int CAP>
+template <int CAP, int F>
 __device__ __forceinline__ void simulate_run(const JobView& J, int32_t g, int32_t w, int32_t run,
                                              int32_t* cnt, int32_t* col, int32_t& total, uint32_t& y0s,
                                              int m0, long long& t1_acc) {
   switch (__ldg(J.fanin_ptr + g + 1) - __ldg(J.fanin_ptr + g)) {
-    case 1: simulate_run_k<1, CAP>(J, g, w, run, cnt, col, total, y0s, m0, t1_acc); break;
-    case 2: simulate_run_k<2, CAP>(J, g, w, run, cnt, col, total, y0s, m0, t1_acc); break;
-    case 3: simulate_run_k<3, CAP>(J, g, w, run, cnt, col, total, y0s, m0, t1_acc); break;
-    default: simulate_run_k<4, CAP>(J, g, w, run, cnt, col, total, y0s, m0, t1_acc); break;
+    case 1: simulate_run_k<1, CAP, F>(J, g, w, run, cnt, col, total, y0s, m0, t1_acc); break;
+    case 2: simulate_run_k<2, CAP, F>(J, g, w, run, cnt, col, total, y0s, m0, t1_acc); break;
+    case 3: simulate_run_k<3, CAP, F>(J, g, w, run, cnt, col, total, y0s, m0, t1_acc); break;
+    default: simulate_run_k<4, CAP, F>(J, g, w, run, cnt, col, total, y0s, m0, t1_acc); break;
   }
 }
 
 // One window of one gate straight to global memory (lanes whose edges did
 // not fit their staging column).
-template <int K>
+template <int K, int F>
 __device__ __forceinline__ int32_t simulate_global_k(const JobView& J, int32_t g, int32_t w, int32_t* dst,
                                                      long long limit) {
   GateCtx<K> c;
@@ -459,17 +482,18 @@ __device__ __forceinline__ int32_t simulate_global_k(const JobView& J, int32_t g
   GlobalSink sink{dst, limit};
   int32_t n = 0, t1 = 0;
   uint32_t y0 = 0;
-  run_gate<K>(pin, c.lut, c.gd, c.edit, window_len(J.w0 + w, J.W, J.C, J.L), sink, n, t1, y0);
+  run_gate<K, F>(pin, c.lut, c.gd, c.edit, window_len(J.w0 + w, J.W, J.C, J.L), sink, n, t1, y0);
   return n;
 }
 
+template <int F>
 __device__ __forceinline__ int32_t simulate_global(const JobView& J, int32_t g, int32_t w, int32_t* dst,
                                                    long long limit) {
   switch (__ldg(J.fanin_ptr + g + 1) - __ldg(J.fanin_ptr + g)) {
-    case 1: return simulate_global_k<1>(J, g, w, dst, limit);
-    case 2: return simulate_global_k<2>(J, g, w, dst, limit);
-    case 3: return simulate_global_k<3>(J, g, w, dst, limit);
-    default: return simulate_global_k<4>(J, g, w, dst, limit);
+    case 1: return simulate_global_k<1, F>(J, g, w, dst, limit);
+    case 2: return simulate_global_k<2, F>(J, g, w, dst, limit);
+    case 3: return simulate_global_k<3, F>(J, g, w, dst, limit);
+    default: return simulate_global_k<4, F>(J, g, w, dst, limit);
   }
 }
 
@@ -595,7 +619,7 @@ __device__ __forceinline__ void finish_tile(const JobView& J, const SegView& S, 
 // Linear tiling: 32 lanes x IPT consecutive items of the level in
 // gate-major order (a tile may span gates); each lane fetches its gate's
 // metadata once and reads its fanin records and edges from global memory.
-template <int IPT>
+template <int IPT, int F>
 __device__ __forceinline__ void linear_tile(const JobView& J, const SegView& S, int32_t tile, WarpSmem<IPT>& sm) {
   constexpr int CAP = WarpSmem<IPT>::CAP;
   const int lane = threadIdx.x & 31;
@@ -618,7 +642,7 @@ __device__ __forceinline__ void linear_tile(const JobView& J, const SegView& S, 
       cur_gl = gl;
       acc_t1 = 0;
       const int32_t before = total;
-      simulate_run<CAP>(J, S.gate_begin + gl, w, run, cnt + m, sm.scr + lane, total, y0s, m, acc_t1);
+      simulate_run<CAP, F>(J, S.gate_begin + gl, w, run, cnt + m, sm.scr + lane, total, y0s, m, acc_t1);
       acc_tc = total - before;
       m += run;
       ++gl;
@@ -631,7 +655,7 @@ __device__ __forceinline__ void linear_tile(const JobView& J, const SegView& S, 
                    [&](int32_t* dst, long long o, long long room) {
                      int32_t gl = r0 / J.NW, w = r0 - gl * J.NW;
                      for (int m = 0; m < n_mine; ++m) {
-                       o += simulate_global(J, S.gate_begin + gl, w, dst + o, room - o);
+                       o += simulate_global<F>(J, S.gate_begin + gl, w, dst + o, room - o);
                        if (++w == J.NW) {
                          w = 0;
                          ++gl;
@@ -954,7 +978,13 @@ __device__ __forceinline__ void linear_tile_pp(const JobView& J, const SegView& 
 // Kernel modes: Algorithm 1 as printed over all of a level's gates (the
 // benchmark kernel, which carries no code of the other modes), pulse limits
 // (with or without a gate list), and a gate list at 100 percent.
+// Modes 4 + F are Algorithm 1 as printed without the features F (above).
 constexpr int kModePlain = 0, kModePulse = 1, kModeCone = 2;
+constexpr int kModeNoWireFilter = 4 + kNoWireFilter, kModeAvgSdf = 4 + kAvgSdf,
+              kModeNoWireAvgSdf = 4 + kNoWireFilter + kAvgSdf;
+__host__ __device__ constexpr int features_of(int mode) { return mode >= 4 ? mode - 4 : 0; }
+// modes whose launches may cover a gate list and write to an append region
+__host__ __device__ constexpr bool lists_of(int mode) { return mode == kModePulse || mode == kModeCone; }
 
 template <int K, int IPT, int MODE>
 __device__ __forceinline__ void wide_tile_k(const JobView& J, const SegView& S, const GateDesc& d, int32_t g,
@@ -1097,7 +1127,7 @@ __device__ __forceinline__ void wide_tile_k(const JobView& J, const SegView& S, 
       WarpSink<CAP> sink{sm.scr + lane, 0};
       int32_t t1 = 0;
       uint32_t y0 = 0;
-      run_gate<K>(pin, lut, gd, edit, window_len(J.w0 + wb + wl, J.W, J.C, J.L), sink, c, t1, y0);
+      run_gate<K, features_of(MODE)>(pin, lut, gd, edit, window_len(J.w0 + wb + wl, J.W, J.C, J.L), sink, c, t1, y0);
       acc_t1 += t1;
       sm.omet[wl] = (uint16_t)(min(c, kMaxCount) | (int32_t)(y0 << 15));
       if (c > kMaxCount) atomicOr(J.status, kStOffset);
@@ -1123,7 +1153,7 @@ __device__ __forceinline__ void wide_tile_k(const JobView& J, const SegView& S, 
   const long long lbase = __ldg(J.lvl_base + S.level);
   // where the launch's runs go: the level's range, or the append region
   long long obase = lbase;
-  if constexpr (MODE != kModePlain) obase = S.append_in ? __ldg(S.append_in) : lbase;
+  if constexpr (lists_of(MODE)) obase = S.append_in ? __ldg(S.append_in) : lbase;
   unsigned long long old = 0;
   if (lane == 0) old = atomicAdd(S.counters, (1ull << kTileShift) + (unsigned long long)out_n);
   {
@@ -1139,7 +1169,7 @@ __device__ __forceinline__ void wide_tile_k(const JobView& J, const SegView& S, 
     if ((long long)(old >> kTileShift) == (long long)S.n_tiles - 1) {
       const long long tot = start + out_n;
       if (tot > 0x7fffffffll) atomicOr(J.status, kStOffset);
-      if (MODE != kModePlain && S.append_in) *S.append_out = obase + tot;
+      if (lists_of(MODE) && S.append_in) *S.append_out = obase + tot;
       else J.lvl_base[S.level + 1] = lbase + tot;
       if (obase + tot > J.capacity) atomicOr(J.status, kStCapacity);
     }
@@ -1181,7 +1211,7 @@ __device__ __forceinline__ void wide_tile_k(const JobView& J, const SegView& S, 
       GlobalSink sink{dst + at, room - at};
       int32_t c = 0, t1 = 0;
       uint32_t y0 = 0;
-      run_gate<K>(pin, lut, gd, edit, window_len(J.w0 + wb + wl, J.W, J.C, J.L), sink, c, t1, y0);
+      run_gate<K, features_of(MODE)>(pin, lut, gd, edit, window_len(J.w0 + wb + wl, J.W, J.C, J.L), sink, c, t1, y0);
     }
   }
 
@@ -1202,7 +1232,7 @@ __device__ __forceinline__ void wide_tile(const JobView& J, const SegView& S, in
   const int32_t tg = tile - gl * J.T;
   const int32_t n = min(TW, J.NW - tg * TW);
   int32_t g = S.gate_begin + gl;
-  if constexpr (MODE != kModePlain) {
+  if constexpr (lists_of(MODE)) {
     if (S.gate_list) g = __ldg(S.gate_list + gl);
   }
   GateDesc d;
@@ -1219,7 +1249,7 @@ template <int IPT, int MODE>
 __device__ __forceinline__ void propagate_warp(const JobView& J, const SegView& S, int32_t tile, WarpSmem<IPT>& sm) {
   if (J.T > 0) wide_tile<IPT, MODE>(J, S, tile, sm);
   else if constexpr (MODE == kModePulse) linear_tile_pp<IPT>(J, S, tile);
-  else linear_tile<IPT>(J, S, tile, sm);
+  else linear_tile<IPT, features_of(MODE)>(J, S, tile, sm);
 }
 
 // Blocks per SM the launch bounds ask for: as many as the per-warp shared
@@ -1347,6 +1377,17 @@ inline bool launch_variant_pp(int nt, int ipt, SingleLaunchMode<kModePulse>& lau
     case 256 * 16 + 2: launch.template go<256, 2>(); return true;
     case 256 * 16 + 4: launch.template go<256, 4>(); return true;
     case 128 * 16 + 8: launch.template go<128, 8>(); return true;
+    default: return false;
+  }
+}
+
+// Kernels without some features (the paper's cost comparison): 256 x 4 and
+// 256 x 1.
+template <int MODE>
+inline bool launch_variant_features(int ipt, SingleLaunchMode<MODE>& launch) {
+  switch (ipt) {
+    case 1: launch.template go<256, 1>(); return true;
+    case 4: launch.template go<256, 4>(); return true;
     default: return false;
   }
 }

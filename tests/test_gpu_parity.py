@@ -29,8 +29,11 @@ def _built():
 def test_hand_traced(case):
     wl = case_workload(case)
     pulse = (case["pulse"]["gate"], case["pulse"]["wire"]) if "pulse" in case else None
+    f = case.get("features", {})
+    features = (0 if f.get("interconnect_filter", True) else gs.NO_INTERCONNECT_FILTER) | \
+               (0 if f.get("full_sdf", True) else gs.PARTIAL_SDF)
     with gs.Simulator(wl.netlist, wl.delays, wl.stim) as sim:
-        sim.simulate(window_cycles=case["W"], pulse=pulse)
+        sim.simulate(window_cycles=case["W"], pulse=pulse, features=features)
         for e in case["expect"]:
             init, ptr, times = sim.window(e["window"])
             n = e["net"]
