@@ -503,6 +503,41 @@ def run_pulse_mode(args):
     print(json.dumps(line), flush=True)
 
 
+def run_features_mode(args):
+    """The kernel-time cost of two features of Algorithm 1 on the benchmark
+    workload, as the paper measures it (Section 5, Table "features"): the
+    full kernel against the kernel without the interconnect inertial filter,
+    and against that without full SDF either (one averaged delay per arc
+    and output edge).  Same launch shape, same stimulus; the steps of the
+    three kernels are interleaved so that clock drift hits them alike."""
+    import gen
+    import paper_2203_06117_gb300 as gs
+    gs.build()
+    wl = gen.make_workload(WORKLOAD, seed=SEED, num_cycles=args.cycles or None)
+    G, C = wl.netlist.num_gates, wl.stim.num_cycles
+    variants = [("full features", 0), ("no interconnect filter", gs.NO_INTERCONNECT_FILTER),
+                ("no interconnect filter + partial SDF", gs.NO_INTERCONNECT_FILTER | gs.PARTIAL_SDF)]
+    ms = {name: [] for name, _ in variants}
+    edges = {}
+    with gs.Simulator(wl.netlist, wl.delays, wl.stim) as sim:
+        for k in range(args.warmup + args.steps):
+            for name, mask in variants:
+                sim.simulate(window_cycles=1, tile_items=256, items_per_thread=4, time_kernels=1, features=mask)
+                if k >= args.warmup:
+                    ms[name].append(sim.stats()["prop_ms"])
+                edges[name] = int(sim.stats()["edges"])
+    full = statistics.median(ms["full features"])
+    rows = [{"kernel": name, "prop_ms": statistics.median(ms[name]), "edges": edges[name],
+             "gate_cycles_per_s": G * C / (statistics.median(ms[name]) / 1e3),
+             "overhead_of_full_kernel": full / statistics.median(ms[name]) - 1.0} for name, _ in variants]
+    line = {"metric": "kernel-time overhead of interconnect filtering and full SDF (fraction of the reduced kernel)",
+            "value": rows[-1]["overhead_of_full_kernel"], "unit": "fraction", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": full, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": f"mid: {G} gates x {C} cycles, 256 x 4 launch shape"}, "kernels": rows}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -521,7 +556,7 @@ def main():
                     help="host processes of the reference arm (0: every core)")
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--workload", default="mid", choices=["mid", "batched", "served", "ingest", "resim", "pulse"],
+    ap.add_argument("--workload", default="mid", choices=["mid", "batched", "served", "ingest", "resim", "pulse", "features"],
                     help="mid = the headline single-job benchmark; batched / served = the "
                          "multi-job engine against the plain per-job path")
     ap.add_argument("--scale", type=float, default=1.0, help="shrink batched/served workloads")
@@ -540,6 +575,8 @@ def main():
         return run_resim_mode(args)
     if args.workload == "pulse":
         return run_pulse_mode(args)
+    if args.workload == "features":
+        return run_features_mode(args)
     world, rank, local = dist_setup()
     if args.impl == "reference":
         run_reference(args, world, rank)
@@ -614,8 +651,7 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-        "config": dict(_config(args), cycles=C, tile_threads=st["tile_threads"],
-                       items_per_thread=st["items_per_thread"]),
+        "config": dict(_config(args), cycles=C),
         "e2e": {"value": units * world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h)},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -634,7 +670,8 @@ def main():
         "clocks": {k: clocks[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")},
         "gpu_launches": int(launches),
         "detail": {"edges_per_step": int(edges), "host_s": host_s, "clock_samples": clocks["samples"],
-                   "saif_tc_total": int(saif[2].sum())},
+                   "saif_tc_total": int(saif[2].sum()), "tile_threads": st["tile_threads"],
+                   "items_per_thread": st["items_per_thread"]},
     }
     print(json.dumps(line), flush=True)
 
