@@ -395,7 +395,7 @@ typedef struct gatspi_engine_opts {
                           this many (gate, window) items per level on
                           average: enough to fill the GPU in one launch,
                           few enough that a step's levels stay in L2;
-                          0 = 2^25 */
+                          0 = 2^24 */
 } gatspi_engine_opts;
 
 typedef struct gatspi_engine_stats {
@@ -409,6 +409,9 @@ typedef struct gatspi_engine_stats {
   int32_t queued;         /* parts waiting for admission now */
   double host_ms;         /* host time spent inside gatspi_engine_step */
   double wait_ms;         /* of which blocked waiting for the device */
+  double prop_ms;         /* device time of the steps' propagation launches
+                             (CUDA events around each step's launches; steps
+                             still in flight are counted once they finish) */
 } gatspi_engine_stats;
 
 /* Job states reported by gatspi_engine_poll. */

@@ -100,7 +100,7 @@ class gatspi_engine_stats(ctypes.Structure):
                 ("parts_done", ctypes.c_int64), ("parts_retried", ctypes.c_int64),
                 ("items", ctypes.c_int64), ("bytes_peak", ctypes.c_int64),
                 ("active", ctypes.c_int32), ("queued", ctypes.c_int32),
-                ("host_ms", ctypes.c_double), ("wait_ms", ctypes.c_double)]
+                ("host_ms", ctypes.c_double), ("wait_ms", ctypes.c_double), ("prop_ms", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -124,6 +124,9 @@ struct gatspi_engine {
   PartResult* h_results = nullptr;
   std::vector<int32_t> free_slots;
   std::vector<cudaEvent_t> free_events;
+  // device time of each step's launches: event pairs in flight, oldest first
+  std::deque<std::pair<cudaEvent_t, cudaEvent_t>> step_ev;
+  std::vector<cudaEvent_t> spare_ev;
   gatspi_engine_stats stats{};
 };
 
@@ -315,6 +318,35 @@ int batch_edges(gatspi_engine* eng, EJob& j, int32_t c0, int32_t c1, int64_t* l0
   return GATSPI_OK;
 }
 
+// Add the device time of finished steps to the statistics (`all`: wait for
+// the ones still in flight).
+int harvest_steps(gatspi_engine* eng, bool all) {
+  while (!eng->step_ev.empty()) {
+    auto pr = eng->step_ev.front();
+    if (all) ECK(cudaEventSynchronize(pr.second));
+    const cudaError_t q = cudaEventQuery(pr.second);
+    if (q == cudaErrorNotReady) break;
+    if (q != cudaSuccess) return efail(eng, GATSPI_ECUDA, std::string("step event: ") + cudaGetErrorString(q));
+    float ms = 0.f;
+    ECK(cudaEventElapsedTime(&ms, pr.first, pr.second));
+    eng->stats.prop_ms += ms;
+    eng->step_ev.pop_front();
+    eng->spare_ev.push_back(pr.first);
+    eng->spare_ev.push_back(pr.second);
+  }
+  return GATSPI_OK;
+}
+
+int step_event(gatspi_engine* eng, cudaEvent_t* ev) {
+  if (!eng->spare_ev.empty()) {
+    *ev = eng->spare_ev.back();
+    eng->spare_ev.pop_back();
+    return GATSPI_OK;
+  }
+  ECK(cudaEventCreate(ev));
+  return GATSPI_OK;
+}
+
 int retire(gatspi_engine* eng, bool wait_one) {
   bool waited = false;
   for (size_t k = 0; k < eng->finishing.size();) {
@@ -429,7 +461,7 @@ int gatspi_engine_create(gatspi_engine** out, int device, size_t arena_bytes, co
     eng->tile = tile_items_of(ipt);
     if (!eng->opts.max_active) eng->opts.max_active = 1024;
     if (!eng->opts.part_items) eng->opts.part_items = 1ll << 30;
-    if (!eng->opts.step_items) eng->opts.step_items = 1ll << 25;
+    if (!eng->opts.step_items) eng->opts.step_items = 1ll << 24;  // the best of 2^24..2^28 measured on the batched stream
     if (cudaSetDevice(device) != cudaSuccess ||
         cudaStreamCreateWithFlags(&eng->stream, cudaStreamNonBlocking) != cudaSuccess ||
         cudaStreamCreateWithFlags(&eng->upload, cudaStreamNonBlocking) != cudaSuccess ||
@@ -482,6 +514,11 @@ int gatspi_engine_destroy(gatspi_engine* eng) {
       if (eng->stage_ev[k]) cudaEventDestroy(eng->stage_ev[k]);
     }
     for (auto e : eng->free_events) cudaEventDestroy(e);
+    for (auto& pr : eng->step_ev) {
+      cudaEventDestroy(pr.first);
+      cudaEventDestroy(pr.second);
+    }
+    for (auto e : eng->spare_ev) cudaEventDestroy(e);
     dfree(eng->d_stage);
     dfree(eng->d_counter);
     if (eng->h_results) cudaFreeHost(eng->h_results);
@@ -726,6 +763,10 @@ static int engine_step_impl(gatspi_engine* eng, int32_t* active_out, int32_t* qu
   // 4. launches: the propagation step for parts already past level 0, then
   // level 0 of the admitted parts
   if (tiles > 0) {
+    if ((rc = harvest_steps(eng, false))) return rc;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    if ((rc = step_event(eng, &ev0)) || (rc = step_event(eng, &ev1))) return rc;
+    ECK(cudaEventRecord(ev0, eng->stream));
     // one launch per kMaxSegs segments, each with its own tile counter
     const size_t n_launch = (segs.size() + kMaxSegs - 1) / kMaxSegs;
     ECK(cudaMemsetAsync(eng->d_counter, 0, sizeof(int32_t) * n_launch, eng->stream));
@@ -749,6 +790,8 @@ static int engine_step_impl(gatspi_engine* eng, int32_t* active_out, int32_t* qu
       ECK(cudaGetLastError());
       eng->stats.kernel_launches++;
     }
+    ECK(cudaEventRecord(ev1, eng->stream));
+    eng->step_ev.emplace_back(ev0, ev1);
     eng->stats.steps++;
   }
   for (size_t k = 0; k < admitted.size(); ++k) {
@@ -920,6 +963,9 @@ int gatspi_engine_release(gatspi_engine* eng, int64_t job_id) {
 int gatspi_engine_get_stats(gatspi_engine* eng, gatspi_engine_stats* out) {
   return guarded(eng, [&]() -> int {
     if (!eng || !out) return GATSPI_EINVAL;
+    ECK(cudaSetDevice(eng->device));
+    const int rc = harvest_steps(eng, false);
+    if (rc) return rc;
     *out = eng->stats;
     return GATSPI_OK;
   });
