@@ -306,7 +306,12 @@ def run_batched_mode(args):
     work = sum(nets[s["netlist"]].netlist.num_gates * s["stim"].num_cycles for s in specs)
     reqs = [serve.Request.from_spec(s) for s in specs]
     opts = dict(tile_items=args.tile or 256, items_per_thread=args.ipt or 4)
-    eopts = dict(opts, step_items=args.step_items)
+    tuning = None
+    if args.tile or args.ipt or args.step_items:
+        eopts = dict(opts, step_items=args.step_items)
+    else:  # the engine autotuner on a sample of the stream (outside the timed runs)
+        eopts, timings = serve.autotune_engine(nets, reqs)
+        tuning = {"chosen": eopts, "candidates_ms": [[round(t, 1), o] for t, o in timings]}
     serve.run_batched(nets, reqs, keep_results=False, **eopts)         # warm-up
     t_b = []
     for _ in range(args.steps):
@@ -325,7 +330,9 @@ def run_batched_mode(args):
                        "jobs": len(reqs), "gate_cycles": int(work),
                        "gates": [n.netlist.num_gates for n in nets]},
             "plain_loop": {"value": work / tp, "ms": tp * 1e3},
-            "speedup_vs_plain": tp / tb, "saif_bit_exact_vs_plain": exact, "engine": st}
+            "speedup_vs_plain": tp / tb, "saif_bit_exact_vs_plain": exact, "engine": st,
+            "engine_options": eopts, "autotune": tuning,
+            "repeats_ms": {"engine": [round(t * 1e3, 1) for t in t_b], "plain": [round(t * 1e3, 1) for t in t_p]}}
     print(json.dumps(line), flush=True)
 
 

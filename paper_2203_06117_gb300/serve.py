@@ -79,6 +79,41 @@ def run_batched(netlists, reqs, keep_results=True, **engine_opts):
         return dt, eng.stats()
 
 
+# launch shapes (threads x windows per thread) and admission sizes (step
+# items) the engine autotuner times; the kernel has one merge strategy
+TUNE_SHAPES = ((256, 4), (128, 8), (256, 2))
+TUNE_STEPS = (1 << 23, 1 << 24, 1 << 25, 1 << 26)
+_TUNED = {}
+
+
+def _mix_key(netlists):
+    return tuple((w.netlist.num_inputs, w.netlist.num_gates, int(w.netlist.fanin_ptr[-1])) for w in netlists)
+
+
+def autotune_engine(netlists, reqs, sample=16, shapes=TUNE_SHAPES, steps=TUNE_STEPS, cache=_TUNED):
+    """Engine options for a netlist mix: every (launch shape, step items)
+    pair is timed on a sample of the stream's jobs (every k-th job, so that
+    sizes and activities stay representative; one warm-up run each), and the
+    fastest is kept.  The choice is cached per netlist mix (inputs, gates
+    and pins of each netlist), so later streams over the same mix reuse it.
+    Returns (options, timings in ms per candidate)."""
+    key = _mix_key(netlists)
+    if key in cache:
+        return dict(cache[key][0]), cache[key][1]
+    k = max(1, len(reqs) // sample)
+    pick = [Request(0.0, r.netlist, r.stim, r.window_cycles, r.edit_gate, r.edit_delta) for r in reqs[::k]]
+    timings = []
+    for nt, ipt in shapes:
+        for si in steps:
+            opts = dict(tile_items=nt, items_per_thread=ipt, step_items=si)
+            run_batched(netlists, pick, keep_results=False, **opts)
+            dt, _ = run_batched(netlists, pick, keep_results=False, **opts)
+            timings.append((dt * 1e3, opts))
+    best = min(timings, key=lambda x: x[0])[1]
+    cache[key] = (best, timings)
+    return dict(best), timings
+
+
 def run_plain_loop(netlists, reqs, keep_results=True, tile_items=256, items_per_thread=4):
     """The single-job path, one job after the other (netlists resident), with
     the engine's default launch shape (no per-netlist autotuning inside the

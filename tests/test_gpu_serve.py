@@ -41,3 +41,25 @@ def test_served_stream_equals_alone():
     serve.run_served_plain(nets, reqs)
     for k, (a, r) in enumerate(zip(mixed, reqs)):
         assert _same(a, r.result), f"request {k}"
+
+
+def test_engine_autotuner_picks_a_timed_candidate_and_caches_it():
+    """The engine autotuner times every (launch shape, step items) candidate
+    on a sample of the stream, returns the fastest, and reuses its choice for
+    the same netlist mix; jobs run with the chosen options give the same SAIF
+    as the plain path."""
+    nets, specs = gen.batched_workload(seed=5, n_jobs=12, n_netlists=3, scale=0.02)
+    reqs = [serve.Request.from_spec(s) for s in specs]
+    cache = {}
+    shapes, steps = ((256, 4), (128, 8)), (1 << 20, 1 << 24)
+    opts, timings = serve.autotune_engine(nets, reqs, sample=6, shapes=shapes, steps=steps, cache=cache)
+    assert len(timings) == 4
+    assert opts == min(timings, key=lambda x: x[0])[1]
+    assert (opts["tile_items"], opts["items_per_thread"]) in shapes and opts["step_items"] in steps
+    again, _ = serve.autotune_engine(nets, reqs, sample=6, shapes=shapes, steps=steps, cache=cache)
+    assert again == opts and len(cache) == 1
+    serve.run_batched(nets, reqs, **opts)
+    batched = [r.result for r in reqs]
+    serve.run_plain_loop(nets, reqs)
+    for k, (a, r) in enumerate(zip(batched, reqs)):
+        assert _same(a, r.result), f"job {k}"
