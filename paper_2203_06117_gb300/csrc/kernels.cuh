@@ -1058,7 +1058,13 @@ __device__ __forceinline__ void wide_tile_k(const JobView& J, const SegView& S, 
     if (lim[i] > 0) run_starts<IPT>(mv[i], lane, n, lim[i], sm.sstart[i]);
   }
 
-  // 2. settle quiet windows, list the others (window order: k-major, lane-minor)
+  // 2. settle the windows whose output cannot change, list the others
+  // (window order: k-major, lane-minor).  A window's output cannot change
+  // when no pin has an edge, and also when the truth table is constant on
+  // every input combination its switching pins can reach from their start
+  // values (the other pins fixed): then every event of Algorithm 1 finds
+  // the output value unchanged, so the window keeps its start value and has
+  // no edge, whatever the arrival times and delays.
   const uint32_t lut = d.lut;
   const uint32_t lt_mask = (1u << lane) - 1u;
   long long acc_t1 = 0;
@@ -1067,13 +1073,22 @@ __device__ __forceinline__ void wide_tile_k(const JobView& J, const SegView& S, 
   for (int k = 0; k < IPT; ++k) {
     const int32_t j = k * 32 + lane;
     const bool valid = j < n;
-    uint32_t col = 0, any = 0;
+    uint32_t col = 0, sw = 0;  // start values; pins with edges
 #pragma unroll
     for (int i = 0; i < K; ++i) {
       col |= (mv[i][k] >> 15) << i;
-      any |= mv[i][k] & (uint32_t)kMaxCount;
+      sw |= ((mv[i][k] & (uint32_t)kMaxCount) != 0u ? 1u : 0u) << i;
     }
-    const bool act = valid && any != 0u;
+    // the reachable combinations as a set of truth-table columns: each
+    // switching pin i doubles the set by its mirror image in bit i
+    uint32_t cube = 1u << col;
+#pragma unroll
+    for (int i = 0; i < K; ++i) {
+      constexpr uint32_t kLow[4] = {0x5555u, 0x3333u, 0x0f0fu, 0x00ffu};  // columns with bit i clear
+      if ((sw >> i) & 1u) cube |= ((cube & kLow[i]) << (1 << i)) | ((cube >> (1 << i)) & kLow[i]);
+    }
+    const uint32_t hit = lut & cube;
+    const bool act = valid && sw != 0u && hit != 0u && hit != cube;
     const uint32_t amask = __ballot_sync(0xffffffffu, act);
     if (act) {
       sm.list[n_act + __popc(amask & lt_mask)] = (uint8_t)j;
