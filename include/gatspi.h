@@ -136,7 +136,9 @@ typedef struct gatspi_stats {
   int64_t kernel_launches; /* kernels of this library launched */
   int64_t prop_launches;   /* propagation-kernel launches */
   int64_t items;           /* (gate, window) items simulated */
-  int64_t edges;           /* waveform edges stored, all nets and windows */
+  int64_t edges;           /* waveform store entries used, all nets and windows: the
+                              edge count at 100 percent; with pulse limits it also
+                              counts the unused rest of each tile's claim */
   int64_t algo_bytes;      /* algorithmic bytes of the propagation kernels:
                               per (gate, window) item and fanin pin a 2-byte
                               record read, per item a 2-byte record written;
