@@ -52,8 +52,9 @@ def _peaks():
 
 
 def _traffic(tile_threads, items_per_thread):
-    """DRAM bytes per propagation launch from the committed ncu summary, or
-    None once the kernel source or the launch shape differs from the one the
+    """DRAM bytes per level (the level's propagation launches: the pair
+    kernel's and propagate_kernel's) from the committed ncu summary, or None
+    once the kernel source or the launch shape differs from the one the
     counters were taken on."""
     import hashlib
     try:
@@ -68,7 +69,7 @@ def _traffic(tile_threads, items_per_thread):
         if (fields.get("kernels_cuh_sha256") != digest or int(fields["tile_threads"]) != tile_threads
                 or int(fields["items_per_thread"]) != items_per_thread):
             return None
-        return int(fields["traffic_bytes_per_launch"])
+        return int(fields["traffic_bytes_per_level"])
     except (OSError, KeyError, ValueError):
         return None
 
@@ -670,7 +671,8 @@ def main():
                      "traffic": _traffic(st["tile_threads"], st["items_per_thread"])
                      if WORKLOAD == "mid" and not args.cycles else None,
                      "peak_kind": peak_kind,
-                     "kernel": "propagate_kernel",
+                     "kernel": "propagate_kernel + propagate_pair_kernel (one level)",
+                     "traffic_per": "level",
                      "algo_bytes_per_step": int(format_step),
                      "bytes_per_unit": "4*sum_pins(2+e_pin) + 4*(2+e_out) + 8 per (gate, cycle)",
                      "layout_bytes_per_step": int(algo[-1]),

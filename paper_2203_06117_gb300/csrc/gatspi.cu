@@ -54,6 +54,8 @@ struct gatspi_ctx {
   std::vector<uint16_t> lut;
   std::vector<int32_t> lvl_gate_begin;  // [D+2]: gates of level l (l >= 1) are
                                         // lvl_gate_begin[l] .. lvl_gate_begin[l+1]
+  std::vector<int32_t> lvl_split;       // [D+2]: the level's gates of at most two
+                                        // pins are lvl_gate_begin[l] .. lvl_split[l]
   std::vector<int64_t> fanout;          // pins driven by each internal net
   int32_t max_gate_delay = 0, max_wire_delay = 0;
   bool have_netlist = false, have_delays = false, have_stim = false, have_result = false;
@@ -238,7 +240,7 @@ bool plan_batch(gatspi_ctx* c, int32_t NW, int ipt, size_t* need_fixed) {
   const int64_t o_lvl = off; off = align_up(off + (c->D + 2) * 8);
   const int64_t o_scr = off;
   const int64_t o_cnt = align_up(o_scr + (int64_t)(c->D + 2) * 8);
-  off = align_up(o_cnt + (c->D + 2) * 4);
+  off = align_up(o_cnt + 2 * (c->D + 2) * 4);  // two launches' tile counters per level
   c->scratch_bytes = (size_t)(off - o_scr);
   const int64_t o_times = off;
   *need_fixed = (size_t)o_times;
@@ -278,7 +280,7 @@ size_t fixed_bytes(const gatspi_ctx* c, int32_t NW, int ipt) {
   const int32_t TW = tile_items_of(ipt);
   const int64_t T = (NW + TW - 1) / TW;
   return (size_t)(align_up(wide_tiling(NW, ipt) ? N * T * 8 : N * NW * 4) + align_up(N * NW * 2) + align_up((c->D + 2) * 8) +
-                  align_up((int64_t)(c->D + 2) * 8) + align_up((c->D + 2) * 4) + 4096);
+                  align_up((int64_t)(c->D + 2) * 8) + align_up(2 * (c->D + 2) * 4) + 4096);
 }
 
 // The edit as one delta per internal gate (all zero: empty vector).
@@ -393,6 +395,7 @@ int gatspi_load_netlist(gatspi_ctx* ctx, int32_t num_inputs, int32_t num_gates,
     ctx->net_level = std::move(r.net_level);
     ctx->lut = std::move(r.lut);
     ctx->lvl_gate_begin = std::move(r.lvl_gate_begin);
+    ctx->lvl_split = std::move(r.lvl_split);
     ctx->fanout = std::move(r.fanout);
     int rc;
     if (!r.gate_desc.empty()) {
@@ -731,6 +734,22 @@ int simulate_impl(gatspi_ctx* ctx, const gatspi_opts* opts) {
     for (int32_t i = 0; i < ctx->I; ++i) ctx->h_in_prefix[i] = in_prefix[i];
     const bool record_first = o.time_kernels && !first_recorded;
     cudaError_t smem_err = cudaSuccess;  // a propagation kernel could not opt in to its shared memory
+    // Algorithm 1 as printed over gate-aligned tiles: a level's gates of at
+    // most two pins run in the pair kernel where it is compiled, when they
+    // make enough tiles that a second launch's last partial wave costs less
+    // than the pair kernel saves
+    const bool split = !pp && !feat && ctx->batch_T > 0 && pair_variant_compiled(nt, ipt);
+    std::vector<int32_t> pair_gates((size_t)ctx->D + 2, 0);
+    int32_t pair_launches = 0, rest_launches = ctx->D;
+    if (split) {
+      for (int32_t l = 1; l <= ctx->D; ++l) {
+        const int32_t np = ctx->lvl_split[l] - ctx->lvl_gate_begin[l];
+        if ((int64_t)np * ctx->batch_T < kPairMinTiles) continue;
+        pair_gates[l] = np;
+        ++pair_launches;
+        if (ctx->lvl_split[l] == ctx->lvl_gate_begin[l + 1]) --rest_launches;
+      }
+    }
     // everything the batch puts on the stream; captured into a CUDA graph
     // and replayed when the same batch comes again (repeated simulations of
     // one stimulus), launched eagerly otherwise.  Timing events are recorded
@@ -771,8 +790,28 @@ int simulate_impl(gatspi_ctx* ctx, const gatspi_opts* opts) {
         p.seg.n_items = (ctx->lvl_gate_begin[l + 1] - ctx->lvl_gate_begin[l]) * nw;
         p.seg.n_tiles = (int32_t)level_tiles(ctx->lvl_gate_begin[l + 1] - ctx->lvl_gate_begin[l], nw, ipt);
         p.tile_counter = ctx->d_tile_counter + l;
+        p.n_tiles = p.seg.n_tiles;
         if (o.time_kernels && (e = rec(ctx->ev[2 * l]))) return e;
-        if (pp) {
+        const int32_t n_pair = pair_gates[l];
+        if (n_pair > 0) {
+          // the level's gates of at most two pins in the pair kernel, the
+          // rest after them; both launches count into the level's counter
+          PropParams q = p;
+          q.n_tiles = n_pair * ctx->batch_T;
+          PairLaunch go{&q, ctx->stream};
+          go.go();
+          if ((e = go.err)) {
+            smem_err = e;
+            return e;
+          }
+          if ((e = cudaGetLastError())) return e;
+          p.seg.gate_begin = ctx->lvl_split[l];
+          p.n_tiles = p.seg.n_tiles - q.n_tiles;
+          p.tile_counter = ctx->d_tile_counter + (ctx->D + 2) + l;
+        }
+        if (p.n_tiles == 0) {
+          e = cudaSuccess;  // every gate of the level went to the pair kernel
+        } else if (pp) {
           SingleLaunchMode<kModePulse> go{&p, ctx->stream};
           launch_variant_pp(nt, ipt, go);
           e = go.err;
@@ -862,8 +901,8 @@ int simulate_impl(gatspi_ctx* ctx, const gatspi_opts* opts) {
       ctx->eager_feat = feat;
     }
     if (record_first) first_recorded = true;
-    st.kernel_launches += 1 + ctx->D + (o.digest ? 1 : 0);
-    st.prop_launches += ctx->D;
+    st.kernel_launches += 1 + rest_launches + pair_launches + (o.digest ? 1 : 0);
+    st.prop_launches += rest_launches + pair_launches;
     st.items += (int64_t)ctx->G * nw;
     CK(cudaStreamSynchronize(ctx->stream));
     const int32_t status = (int32_t)ctx->h_ret[0];
@@ -1135,6 +1174,7 @@ int gatspi_resimulate_edit(gatspi_ctx* ctx, int32_t n_edits, const int32_t* edit
       p.seg.gate_begin = ctx->lvl_gate_begin[l];
       p.seg.n_items = nc * nw;
       p.seg.n_tiles = nc * T;
+      p.n_tiles = p.seg.n_tiles;
       p.seg.gate_list = ctx->d_cone + lvl_off[l];
       p.seg.append_in = ctx->d_append + (k & 1);
       p.seg.append_out = ctx->d_append + ((k + 1) & 1);

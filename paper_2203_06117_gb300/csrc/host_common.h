@@ -29,6 +29,8 @@ struct Prepared {
   std::vector<uint16_t> lut;            // [G]
   std::vector<int32_t> lvl_gate_begin;  // [D+2]: level l >= 1 holds internal
                                         // gates lvl_gate_begin[l] .. [l+1]
+  std::vector<int32_t> lvl_split;       // [D+2]: within level l the gates of at
+                                        // most two pins come first, up to lvl_split[l]
   std::vector<int64_t> fanout;          // pins driven by each internal net
   // Per internal gate, 8 words the propagation kernel fetches in one go:
   // fanin nets (unused pins repeat pin 0's net), first pin, truth table |
@@ -67,13 +69,23 @@ inline std::string prepare_netlist(int32_t I, int32_t G, const int32_t* fanin_pt
   for (int32_t g = 0; g < G; ++g) D = std::max(D, level[(size_t)I + g]);
   r.I = I; r.G = G; r.N = I + G; r.P = P; r.D = D;
   r.lvl_gate_begin.assign(D + 2, 0);
-  for (int32_t g = 0; g < G; ++g) r.lvl_gate_begin[level[(size_t)I + g] + 1]++;
+  r.lvl_split.assign(D + 2, 0);
+  std::vector<int32_t> pairs(D + 2, 0);  // gates of at most two pins per level
+  for (int32_t g = 0; g < G; ++g) {
+    r.lvl_gate_begin[level[(size_t)I + g] + 1]++;
+    if (fanin_ptr[g + 1] - fanin_ptr[g] <= 2) pairs[level[(size_t)I + g]]++;
+  }
   for (int32_t l = 1; l <= D; ++l) r.lvl_gate_begin[l + 1] += r.lvl_gate_begin[l];
-  std::vector<int32_t> fill(r.lvl_gate_begin.begin(), r.lvl_gate_begin.end());
+  for (int32_t l = 0; l <= D + 1; ++l) r.lvl_split[l] = r.lvl_gate_begin[l] + (l <= D ? pairs[l] : 0);
+  // internal order: by level, then gates of at most two pins before the
+  // others (each class in the caller's order)
+  std::vector<int32_t> fill_pair(r.lvl_gate_begin.begin(), r.lvl_gate_begin.end());
+  std::vector<int32_t> fill_rest(r.lvl_split.begin(), r.lvl_split.end());
   r.gate_ext.assign(G, 0);
   r.gate_int.assign(G, 0);
   for (int32_t g = 0; g < G; ++g) {
-    const int32_t j = fill[level[(size_t)I + g]]++;
+    const int32_t lv = level[(size_t)I + g];
+    const int32_t j = fanin_ptr[g + 1] - fanin_ptr[g] <= 2 ? fill_pair[lv]++ : fill_rest[lv]++;
     r.gate_ext[j] = g;
     r.gate_int[g] = j;
   }

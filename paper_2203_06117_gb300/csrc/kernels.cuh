@@ -113,6 +113,9 @@ struct PropParams {
   JobView job;
   SegView seg;
   int32_t* tile_counter;  // zero before the launch
+  int32_t n_tiles;        // tiles of this launch: seg.n_tiles, or the part of
+                          // the level's gates it covers (seg.n_tiles counts the
+                          // whole level, whose last tile publishes its end)
 };
 
 struct MultiSeg {
@@ -503,19 +506,19 @@ __device__ __forceinline__ int32_t simulate_global(const JobView& J, int32_t g, 
 // starts inside the pin's tile run, the run itself (pins share one pool),
 // and the gate's delay tables; and keeps per window its output meta, plus
 // the list of windows that have fanin edges.
-template <int IPT>
+template <int IPT, int KMAX = 4>
 struct WarpSmem {
   static constexpr int TW = 32 * IPT;    // windows (items) per tile
   static constexpr int POOL = 4 * TW;    // fanin edge times staged per tile
   static constexpr int CAP = 8;          // output edges staged per lane (per round)
   static constexpr int OCAP = (2 * TW > CAP * 32) ? 2 * TW : CAP * 32;  // compacted output edges
-  int32_t sstart[4][TW];
+  int32_t sstart[KMAX][TW];
   int32_t spool[POOL];
   int32_t scr[CAP * 32];
   int32_t cmp[OCAP];
   int32_t cnt[TW];     // linear: per-item edge counts; gate-aligned: per-window output offsets
-  int32_t sgd[4][32];  // gate-aligned: the gate's delay tables
-  uint16_t smeta[4][TW];
+  int32_t sgd[KMAX][32];  // gate-aligned: the gate's delay tables
+  uint16_t smeta[KMAX][TW];
   uint16_t omet[TW];
   uint8_t list[TW];
 };
@@ -986,13 +989,14 @@ __host__ __device__ constexpr int features_of(int mode) { return mode >= 4 ? mod
 // modes whose launches may cover a gate list and write to an append region
 __host__ __device__ constexpr bool lists_of(int mode) { return mode == kModePulse || mode == kModeCone; }
 
-template <int K, int IPT, int MODE>
+template <int K, int IPT, int MODE, int KMAX = 4>
 __device__ __forceinline__ void wide_tile_k(const JobView& J, const SegView& S, const GateDesc& d, int32_t g,
-                                            int32_t tg, int32_t n, WarpSmem<IPT>& sm) {
-  constexpr int CAP = WarpSmem<IPT>::CAP;
-  constexpr int POOL = WarpSmem<IPT>::POOL;
-  constexpr int OCAP = WarpSmem<IPT>::OCAP;
-  constexpr int TW = WarpSmem<IPT>::TW;
+                                            int32_t tg, int32_t n, WarpSmem<IPT, KMAX>& sm) {
+  static_assert(K <= KMAX, "the tile body stages at most KMAX pins");
+  constexpr int CAP = WarpSmem<IPT, KMAX>::CAP;
+  constexpr int POOL = WarpSmem<IPT, KMAX>::POOL;
+  constexpr int OCAP = WarpSmem<IPT, KMAX>::OCAP;
+  constexpr int TW = WarpSmem<IPT, KMAX>::TW;
   const int lane = threadIdx.x & 31;
   const int32_t wb = tg * TW;
   const int32_t p0 = d.p0;
@@ -1292,8 +1296,44 @@ __global__ void __launch_bounds__(NT, (min_blocks<NT, IPT>())) propagate_kernel(
   if (threadIdx.x == 0) s_first = atomicAdd(p.tile_counter, NT / 32);
   __syncthreads();
   const int32_t t = s_first + (int32_t)(threadIdx.x >> 5);
-  if (t >= p.seg.n_tiles) return;
+  if (t >= p.n_tiles) return;
   propagate_warp<IPT, MODE>(p.job, p.seg, t, sm[threadIdx.x >> 5]);
+}
+
+// Shared memory of the kernel for gates of at most two pins: two pins
+// staged per tile.
+template <int IPT>
+using PairSmem = WarpSmem<IPT, 2>;
+template <int NT, int IPT>
+__host__ __device__ constexpr int pair_blocks() {
+  return (int)((227u * 1024u) / (sizeof(PairSmem<IPT>) * (NT / 32) + 2048u)) < 1024 / NT
+             ? (int)((227u * 1024u) / (sizeof(PairSmem<IPT>) * (NT / 32) + 2048u))
+             : 1024 / NT;
+}
+
+// Algorithm 1 as printed over gate-aligned tiles of a level's gates of at
+// most two pins (the level's first gates).  The body is the 2-pin one of
+// propagate_kernel; with two pins' staging per warp, four blocks of 256
+// threads fit an SM instead of three, and the registers fit the 64 that
+// four blocks leave.
+template <int NT, int IPT>
+__global__ void __launch_bounds__(NT, (pair_blocks<NT, IPT>())) propagate_pair_kernel(const __grid_constant__ PropParams p) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  PairSmem<IPT>* sm = reinterpret_cast<PairSmem<IPT>*>(smem_raw);
+  __shared__ int32_t s_first;
+  if (threadIdx.x == 0) s_first = atomicAdd(p.tile_counter, NT / 32);
+  __syncthreads();
+  const int32_t t = s_first + (int32_t)(threadIdx.x >> 5);
+  if (t >= p.n_tiles) return;
+  const JobView& J = p.job;
+  constexpr int TW = 32 * IPT;
+  const int32_t gl = t / J.T;
+  const int32_t tg = t - gl * J.T;
+  const int32_t n = min(TW, J.NW - tg * TW);
+  const int32_t g = p.seg.gate_begin + gl;
+  GateDesc d;
+  load_desc(J, g, d);
+  wide_tile_k<2, IPT, kModePlain, 2>(J, p.seg, d, g, tg, n, sm[threadIdx.x >> 5]);
 }
 
 // Several jobs (each at its own level) in one launch: tiles are handed out
@@ -1361,7 +1401,7 @@ struct SingleLaunch {
   void go() {
     static gatspi_host::PerDeviceOnce once;
     if ((err = smem_opt_in(propagate_kernel<NT, IPT>, dyn_smem<NT, IPT>(), once)) != cudaSuccess) return;
-    const unsigned grid = (unsigned)((p->seg.n_tiles + NT / 32 - 1) / (NT / 32));
+    const unsigned grid = (unsigned)((p->n_tiles + NT / 32 - 1) / (NT / 32));
     propagate_kernel<NT, IPT><<<grid, NT, dyn_smem<NT, IPT>(), s>>>(*p);
   }
 };
@@ -1376,8 +1416,31 @@ struct SingleLaunchMode {
   void go() {
     static gatspi_host::PerDeviceOnce once;
     if ((err = smem_opt_in(propagate_kernel<NT, IPT, MODE>, dyn_smem<NT, IPT>(), once)) != cudaSuccess) return;
-    const unsigned grid = (unsigned)((p->seg.n_tiles + NT / 32 - 1) / (NT / 32));
+    const unsigned grid = (unsigned)((p->n_tiles + NT / 32 - 1) / (NT / 32));
     propagate_kernel<NT, IPT, MODE><<<grid, NT, dyn_smem<NT, IPT>(), s>>>(*p);
+  }
+};
+
+// The kernel for gates of at most two pins, compiled for 256 x 4 only (the
+// other launch shapes run those gates in propagate_kernel).
+inline bool pair_variant_compiled(int nt, int ipt) { return nt == 256 && ipt == 4; }
+
+// Fewest tiles of a level's gates of at most two pins for which they get a
+// launch of their own (about seven waves of the pair kernel on 152 SMs):
+// smaller parts stay in the level's one launch.
+constexpr int64_t kPairMinTiles = 32768;
+
+struct PairLaunch {
+  const PropParams* p;
+  cudaStream_t s;
+  cudaError_t err = cudaSuccess;
+  void go() {
+    constexpr int NT = 256, IPT = 4;
+    static gatspi_host::PerDeviceOnce once;
+    const size_t bytes = sizeof(PairSmem<IPT>) * (NT / 32);
+    if ((err = smem_opt_in(propagate_pair_kernel<NT, IPT>, bytes, once)) != cudaSuccess) return;
+    const unsigned grid = (unsigned)((p->n_tiles + NT / 32 - 1) / (NT / 32));
+    propagate_pair_kernel<NT, IPT><<<grid, NT, bytes, s>>>(*p);
   }
 };
 

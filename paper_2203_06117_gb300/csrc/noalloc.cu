@@ -130,6 +130,7 @@ extern "C" int gatspi_propagate_level_noalloc(const gatspi_level_args* a, void* 
   p.seg.gate_begin = a->gate_begin;
   p.seg.n_items = (int32_t)items;
   p.seg.n_tiles = (int32_t)tiles;
+  p.n_tiles = p.seg.n_tiles;
   p.tile_counter = (int32_t*)(scratch + 1);
   SingleLaunch go{&p, s};
   go.go<kNoAllocThreads, kNoAllocItemsPerThread>();
