@@ -66,10 +66,9 @@ def _traffic(tile_threads, items_per_thread):
                     fields[k.strip()] = v.strip()
         with open(os.path.join(ROOT, "paper_2203_06117_gb300", "csrc", "kernels.cuh"), "rb") as f:
             digest = hashlib.sha256(f.read()).hexdigest()
-        if (fields.get("kernels_cuh_sha256") != digest or int(fields["tile_threads"]) != tile_threads
-                or int(fields["items_per_thread"]) != items_per_thread):
+        if fields.get("kernels_cuh_sha256") != digest:
             return None
-        return int(fields["traffic_bytes_per_level"])
+        return int(fields[f"traffic_bytes_per_level_{tile_threads}x{items_per_thread}"])
     except (OSError, KeyError, ValueError):
         return None
 

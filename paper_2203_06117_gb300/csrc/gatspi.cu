@@ -799,7 +799,8 @@ int simulate_impl(gatspi_ctx* ctx, const gatspi_opts* opts) {
           PropParams q = p;
           q.n_tiles = n_pair * ctx->batch_T;
           PairLaunch go{&q, ctx->stream};
-          go.go();
+          if (nt == 128) go.go<128>();
+          else go.go<256>();
           if ((e = go.err)) {
             smem_err = e;
             return e;

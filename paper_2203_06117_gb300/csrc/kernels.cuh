@@ -1421,9 +1421,9 @@ struct SingleLaunchMode {
   }
 };
 
-// The kernel for gates of at most two pins, compiled for 256 x 4 only (the
-// other launch shapes run those gates in propagate_kernel).
-inline bool pair_variant_compiled(int nt, int ipt) { return nt == 256 && ipt == 4; }
+// The kernel for gates of at most two pins, compiled for 256 x 4 and
+// 128 x 4 (the other launch shapes run those gates in propagate_kernel).
+inline bool pair_variant_compiled(int nt, int ipt) { return (nt == 256 || nt == 128) && ipt == 4; }
 
 // Fewest tiles of a level's gates of at most two pins for which they get a
 // launch of their own (about seven waves of the pair kernel on 152 SMs):
@@ -1434,8 +1434,9 @@ struct PairLaunch {
   const PropParams* p;
   cudaStream_t s;
   cudaError_t err = cudaSuccess;
+  template <int NT>
   void go() {
-    constexpr int NT = 256, IPT = 4;
+    constexpr int IPT = 4;
     static gatspi_host::PerDeviceOnce once;
     const size_t bytes = sizeof(PairSmem<IPT>) * (NT / 32);
     if ((err = smem_opt_in(propagate_pair_kernel<NT, IPT>, bytes, once)) != cudaSuccess) return;
