@@ -734,11 +734,11 @@ int simulate_impl(gatspi_ctx* ctx, const gatspi_opts* opts) {
     for (int32_t i = 0; i < ctx->I; ++i) ctx->h_in_prefix[i] = in_prefix[i];
     const bool record_first = o.time_kernels && !first_recorded;
     cudaError_t smem_err = cudaSuccess;  // a propagation kernel could not opt in to its shared memory
-    // Algorithm 1 as printed over gate-aligned tiles: a level's gates of at
-    // most two pins run in the pair kernel where it is compiled, when they
-    // make enough tiles that a second launch's last partial wave costs less
-    // than the pair kernel saves
-    const bool split = !pp && !feat && ctx->batch_T > 0 && pair_variant_compiled(nt, ipt);
+    // Algorithm 1 as printed or without some features, over gate-aligned
+    // tiles: a level's gates of at most two pins run in the pair kernel where
+    // it is compiled, when they make enough tiles that a second launch's last
+    // partial wave costs less than the pair kernel saves
+    const bool split = !pp && ctx->batch_T > 0 && pair_variant_compiled(nt, ipt, feat);
     std::vector<int32_t> pair_gates((size_t)ctx->D + 2, 0);
     int32_t pair_launches = 0, rest_launches = ctx->D;
     if (split) {
@@ -799,8 +799,11 @@ int simulate_impl(gatspi_ctx* ctx, const gatspi_opts* opts) {
           PropParams q = p;
           q.n_tiles = n_pair * ctx->batch_T;
           PairLaunch go{&q, ctx->stream};
-          if (nt == 128) go.go<128>();
-          else go.go<256>();
+          if (feat == GATSPI_NO_INTERCONNECT_FILTER) go.go<256, kModeNoWireFilter>();
+          else if (feat == GATSPI_PARTIAL_SDF) go.go<256, kModeAvgSdf>();
+          else if (feat) go.go<256, kModeNoWireAvgSdf>();
+          else if (nt == 128) go.go<128, kModePlain>();
+          else go.go<256, kModePlain>();
           if ((e = go.err)) {
             smem_err = e;
             return e;

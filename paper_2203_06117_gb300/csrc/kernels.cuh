@@ -1311,12 +1311,12 @@ __host__ __device__ constexpr int pair_blocks() {
              : 1024 / NT;
 }
 
-// Algorithm 1 as printed over gate-aligned tiles of a level's gates of at
-// most two pins (the level's first gates).  The body is the 2-pin one of
-// propagate_kernel; with two pins' staging per warp, four blocks of 256
-// threads fit an SM instead of three, and the registers fit the 64 that
-// four blocks leave.
-template <int NT, int IPT>
+// Algorithm 1 as printed (or without the features of MODE 4 + F) over
+// gate-aligned tiles of a level's gates of at most two pins (the level's
+// first gates).  The body is the 2-pin one of propagate_kernel; with two
+// pins' staging per warp, four blocks of 256 threads fit an SM instead of
+// three, and the registers fit the 64 that four blocks leave.
+template <int NT, int IPT, int MODE = kModePlain>
 __global__ void __launch_bounds__(NT, (pair_blocks<NT, IPT>())) propagate_pair_kernel(const __grid_constant__ PropParams p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   PairSmem<IPT>* sm = reinterpret_cast<PairSmem<IPT>*>(smem_raw);
@@ -1333,7 +1333,8 @@ __global__ void __launch_bounds__(NT, (pair_blocks<NT, IPT>())) propagate_pair_k
   const int32_t g = p.seg.gate_begin + gl;
   GateDesc d;
   load_desc(J, g, d);
-  wide_tile_k<2, IPT, kModePlain, 2>(J, p.seg, d, g, tg, n, sm[threadIdx.x >> 5]);
+  static_assert(!lists_of(MODE), "the pair kernel covers a level's gates, without a gate list");
+  wide_tile_k<2, IPT, MODE, 2>(J, p.seg, d, g, tg, n, sm[threadIdx.x >> 5]);
 }
 
 // Several jobs (each at its own level) in one launch: tiles are handed out
@@ -1421,9 +1422,12 @@ struct SingleLaunchMode {
   }
 };
 
-// The kernel for gates of at most two pins, compiled for 256 x 4 and
-// 128 x 4 (the other launch shapes run those gates in propagate_kernel).
-inline bool pair_variant_compiled(int nt, int ipt) { return (nt == 256 || nt == 128) && ipt == 4; }
+// The kernel for gates of at most two pins: Algorithm 1 as printed at
+// 256 x 4 and 128 x 4, the reduced-feature modes at 256 x 4 (the other
+// launch shapes run those gates in propagate_kernel).
+inline bool pair_variant_compiled(int nt, int ipt, int features) {
+  return ipt == 4 && (nt == 256 || (nt == 128 && features == 0));
+}
 
 // Fewest tiles of a level's gates of at most two pins for which they get a
 // launch of their own (about seven waves of the pair kernel on 152 SMs):
@@ -1434,14 +1438,14 @@ struct PairLaunch {
   const PropParams* p;
   cudaStream_t s;
   cudaError_t err = cudaSuccess;
-  template <int NT>
+  template <int NT, int MODE>
   void go() {
     constexpr int IPT = 4;
     static gatspi_host::PerDeviceOnce once;
     const size_t bytes = sizeof(PairSmem<IPT>) * (NT / 32);
-    if ((err = smem_opt_in(propagate_pair_kernel<NT, IPT>, bytes, once)) != cudaSuccess) return;
+    if ((err = smem_opt_in(propagate_pair_kernel<NT, IPT, MODE>, bytes, once)) != cudaSuccess) return;
     const unsigned grid = (unsigned)((p->n_tiles + NT / 32 - 1) / (NT / 32));
-    propagate_pair_kernel<NT, IPT><<<grid, NT, bytes, s>>>(*p);
+    propagate_pair_kernel<NT, IPT, MODE><<<grid, NT, bytes, s>>>(*p);
   }
 };
 
