@@ -119,7 +119,7 @@ struct gatspi_engine {
   int ring = 0;
   char* d_stage = nullptr;
   size_t d_stage_cap = 0;
-  int32_t* d_counter = nullptr;  // one tile counter per launch of a step
+  int32_t* d_counter = nullptr;  // one tile counter per launch of a step (pair and other launches)
   // pinned per-part result slots
   PartResult* h_results = nullptr;
   std::vector<int32_t> free_slots;
@@ -465,7 +465,7 @@ int gatspi_engine_create(gatspi_engine** out, int device, size_t arena_bytes, co
     if (cudaSetDevice(device) != cudaSuccess ||
         cudaStreamCreateWithFlags(&eng->stream, cudaStreamNonBlocking) != cudaSuccess ||
         cudaStreamCreateWithFlags(&eng->upload, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaMalloc(&eng->d_counter, sizeof(int32_t) * (size_t)(eng->opts.max_active / kMaxSegs + 2)) !=
+        cudaMalloc(&eng->d_counter, sizeof(int32_t) * (size_t)(2 * (eng->opts.max_active / kMaxSegs + 2))) !=
             cudaSuccess ||
         cudaMallocHost(&eng->h_results, sizeof(PartResult) * (size_t)eng->opts.max_active) != cudaSuccess) {
       cudaGetLastError();
@@ -738,7 +738,26 @@ static int engine_step_impl(gatspi_engine* eng, int32_t* active_out, int32_t* qu
     std::memcpy(h + pre_off[k], prefixes[k].data(), prefixes[k].size() * sizeof(long long));
   // levels: admitted parts run level 0 (inputs kernel) in this step and
   // level 1 onwards from the next step
-  std::vector<MultiSeg> segs;
+  // Each (part, level) segment's gates of at most two pins go to the pair
+  // kernel, when the engine's launch shape has one and the step has enough
+  // such tiles for a launch of their own; the rest of each level goes to
+  // propagate_multi_kernel.  Both parts count into the level's counter.
+  const int32_t TW = tile_items_of(eng->ipt);
+  auto tiles_per_gate = [&](const EPart* p) {
+    return wide_tiling(p->nw, eng->ipt) ? (p->nw + TW - 1) / TW : 0;
+  };
+  bool split = pair_variant_compiled(eng->nt, eng->ipt, 0);
+  if (split) {
+    int64_t pair_total = 0;
+    for (EPart* p : stepping) {
+      if (p->level < 1) continue;
+      const ENetlist& nl = *eng->nets[eng->jobs.at(p->job)->net];
+      pair_total += (int64_t)(nl.r.lvl_split[p->level] - nl.r.lvl_gate_begin[p->level]) * tiles_per_gate(p);
+    }
+    split = pair_total >= kPairMinTiles;
+  }
+  std::vector<MultiSeg> segs, pair_segs;
+  std::vector<int32_t> seg_tiles, pair_tiles;  // each segment's tiles in its launch
   int64_t tiles = 0;
   for (EPart* p : stepping) {
     if (p->level < 1) continue;
@@ -754,8 +773,19 @@ static int engine_step_impl(gatspi_engine* eng, int32_t* active_out, int32_t* qu
     s.job = make_view(nl, j, *p);
     s.tile_begin = 0;
     tiles += s.seg.n_tiles;
-    segs.push_back(s);
     eng->stats.items += s.seg.n_items;
+    const int32_t T = tiles_per_gate(p);
+    const int32_t n_pair = split && T > 0 ? nl.r.lvl_split[l] - nl.r.lvl_gate_begin[l] : 0;
+    if (n_pair > 0) {
+      pair_segs.push_back(s);
+      pair_tiles.push_back(n_pair * T);
+      s.seg.gate_begin = nl.r.lvl_split[l];
+    }
+    const int32_t rest = s.seg.n_tiles - n_pair * T;
+    if (rest > 0) {
+      segs.push_back(s);
+      seg_tiles.push_back(rest);
+    }
   }
   if (bytes) ECK(cudaMemcpyAsync(eng->d_stage, h, bytes, cudaMemcpyHostToDevice, eng->stream));
   ECK(cudaEventRecord(eng->stage_ev[slot], eng->stream));
@@ -767,26 +797,41 @@ static int engine_step_impl(gatspi_engine* eng, int32_t* active_out, int32_t* qu
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     if ((rc = step_event(eng, &ev0)) || (rc = step_event(eng, &ev1))) return rc;
     ECK(cudaEventRecord(ev0, eng->stream));
-    // one launch per kMaxSegs segments, each with its own tile counter
+    // one launch per kMaxSegs segments, each with its own tile counter:
+    // the pair launches first, then the others
+    const size_t n_pair_launch = (pair_segs.size() + kMaxSegs - 1) / kMaxSegs;
     const size_t n_launch = (segs.size() + kMaxSegs - 1) / kMaxSegs;
-    ECK(cudaMemsetAsync(eng->d_counter, 0, sizeof(int32_t) * n_launch, eng->stream));
-    for (size_t c = 0; c < n_launch; ++c) {
+    ECK(cudaMemsetAsync(eng->d_counter, 0, sizeof(int32_t) * (n_pair_launch + n_launch), eng->stream));
+    for (size_t c = 0; c < n_pair_launch + n_launch; ++c) {
+      const bool pair = c < n_pair_launch;
+      const std::vector<MultiSeg>& list = pair ? pair_segs : segs;
+      const std::vector<int32_t>& ltiles = pair ? pair_tiles : seg_tiles;
+      const size_t c0 = pair ? c : c - n_pair_launch;
       MultiParams m{};
       int64_t t = 0;
-      for (size_t k = c * kMaxSegs; k < segs.size() && k < (c + 1) * kMaxSegs; ++k) {
+      for (size_t k = c0 * kMaxSegs; k < list.size() && k < (c0 + 1) * kMaxSegs; ++k) {
         MultiSeg& s = m.segs[m.n_segs++];
-        s = segs[k];
+        s = list[k];
         s.tile_begin = (int32_t)t;
-        t += s.seg.n_tiles;
+        t += ltiles[k];
       }
       if (t > 0x7fffff00ll) return efail(eng, GATSPI_ECAPACITY, "too many tiles in one launch");
       m.n_tiles = (int32_t)t;
       m.tile_counter = eng->d_counter + c;
-      MultiLaunch go{&m, eng->stream};
-      launch_variant(eng->nt, eng->ipt, go);
-      if (go.err)
+      cudaError_t err;
+      if (pair) {
+        MultiPairLaunch go{&m, eng->stream};
+        if (eng->nt == 128) go.go<128>();
+        else go.go<256>();
+        err = go.err;
+      } else {
+        MultiLaunch go{&m, eng->stream};
+        launch_variant(eng->nt, eng->ipt, go);
+        err = go.err;
+      }
+      if (err)
         return efail(eng, GATSPI_ECUDA, "enabling the propagation kernel's shared memory on device " +
-                                            std::to_string(eng->device) + " failed: " + cudaGetErrorString(go.err));
+                                            std::to_string(eng->device) + " failed: " + cudaGetErrorString(err));
       ECK(cudaGetLastError());
       eng->stats.kernel_launches++;
     }

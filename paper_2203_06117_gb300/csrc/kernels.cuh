@@ -1337,6 +1337,37 @@ __global__ void __launch_bounds__(NT, (pair_blocks<NT, IPT>())) propagate_pair_k
   wide_tile_k<2, IPT, MODE, 2>(J, p.seg, d, g, tg, n, sm[threadIdx.x >> 5]);
 }
 
+// The pair kernel over several jobs' segments (the gates of at most two pins
+// of each (part, level) segment; propagate_multi_kernel runs the rest of
+// each level, into the same level counters).
+template <int NT, int IPT>
+__global__ void __launch_bounds__(NT, (pair_blocks<NT, IPT>()))
+    propagate_pair_multi_kernel(const __grid_constant__ MultiParams m) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  PairSmem<IPT>* sm = reinterpret_cast<PairSmem<IPT>*>(smem_raw);
+  __shared__ int32_t s_first;
+  if (threadIdx.x == 0) s_first = atomicAdd(m.tile_counter, NT / 32);
+  __syncthreads();
+  const int32_t t = s_first + (int32_t)(threadIdx.x >> 5);
+  if (t >= m.n_tiles) return;
+  int32_t lo = 0, hi = m.n_segs - 1;
+  while (lo < hi) {  // last segment with tile_begin <= t
+    const int32_t mid = (lo + hi + 1) >> 1;
+    if (m.segs[mid].tile_begin <= t) lo = mid; else hi = mid - 1;
+  }
+  const MultiSeg& sg = m.segs[lo];
+  const JobView& J = sg.job;
+  constexpr int TW = 32 * IPT;
+  const int32_t tile = t - sg.tile_begin;
+  const int32_t gl = tile / J.T;
+  const int32_t tg = tile - gl * J.T;
+  const int32_t n = min(TW, J.NW - tg * TW);
+  const int32_t g = sg.seg.gate_begin + gl;
+  GateDesc d;
+  load_desc(J, g, d);
+  wide_tile_k<2, IPT, kModePlain, 2>(J, sg.seg, d, g, tg, n, sm[threadIdx.x >> 5]);
+}
+
 // Several jobs (each at its own level) in one launch: tiles are handed out
 // as above and mapped to (job, level) segments, each segment with its own
 // counters and tiling.
@@ -1446,6 +1477,21 @@ struct PairLaunch {
     if ((err = smem_opt_in(propagate_pair_kernel<NT, IPT, MODE>, bytes, once)) != cudaSuccess) return;
     const unsigned grid = (unsigned)((p->n_tiles + NT / 32 - 1) / (NT / 32));
     propagate_pair_kernel<NT, IPT, MODE><<<grid, NT, bytes, s>>>(*p);
+  }
+};
+
+struct MultiPairLaunch {
+  const MultiParams* m;
+  cudaStream_t s;
+  cudaError_t err = cudaSuccess;
+  template <int NT>
+  void go() {
+    constexpr int IPT = 4;
+    static gatspi_host::PerDeviceOnce once;
+    const size_t bytes = sizeof(PairSmem<IPT>) * (NT / 32);
+    if ((err = smem_opt_in(propagate_pair_multi_kernel<NT, IPT>, bytes, once)) != cudaSuccess) return;
+    const unsigned grid = (unsigned)((m->n_tiles + NT / 32 - 1) / (NT / 32));
+    propagate_pair_multi_kernel<NT, IPT><<<grid, NT, bytes, s>>>(*m);
   }
 };
 
