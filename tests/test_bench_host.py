@@ -41,3 +41,26 @@ def test_clock_samples_summary():
     assert c.summary()["reasons"] == ["hw_slowdown", "hw_thermal_slowdown"]
     c.lines = []
     assert c.summary()["sm_mhz"] is None
+
+
+def test_traffic_record_is_read_per_shape_and_only_for_its_kernel_source(tmp_path, monkeypatch):
+    """The roofline's `traffic` comes from the committed ncu record only while
+    the kernel source hashes to the recorded value, for the launch shapes it
+    lists; otherwise it is null."""
+    import hashlib
+    import os
+    root = tmp_path
+    (root / "profiles").mkdir()
+    src = root / "paper_2203_06117_gb300" / "csrc"
+    src.mkdir(parents=True)
+    (src / "kernels.cuh").write_bytes(b"kernel source")
+    digest = hashlib.sha256(b"kernel source").hexdigest()
+    rec = root / "profiles" / "propagate_kernel_traffic.txt"
+    rec.write_text(f"# comment: a line\nkernels_cuh_sha256: {digest}\ntraffic_bytes_per_level_128x4: 1234\n")
+    monkeypatch.setattr(bench, "ROOT", str(root))
+    assert bench._traffic(128, 4) == 1234
+    assert bench._traffic(256, 4) is None
+    rec.write_text("kernels_cuh_sha256: 00\ntraffic_bytes_per_level_128x4: 1234\n")
+    assert bench._traffic(128, 4) is None
+    os.remove(rec)
+    assert bench._traffic(128, 4) is None
